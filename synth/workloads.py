@@ -1,0 +1,85 @@
+"""The five synthetic workloads of the hot path, by name and size (shared inputs only).
+
+Each workload is a dict: mesh (V, F), time step dt, number of steps Nt,
+coupling alpha and the plane-wave batch.  Names state what they are:
+
+  sphere480_fp64     icosphere level 2 (320 tri / 480 edges), dt 0.2, 300 steps, x-pol along +z,
+                     sigma 2, t0 8; FP64 path, direct solve.
+  torus864_fp32      torus R 1, r 0.4, 24x12 (576 tri / 864 edges), genus 1, dt 2.0, 1000 steps,
+                     same pulse; FP32 history.
+  sphere7680_r64     icosphere level 4 (5120 tri / 7680 edges), 64 Fibonacci directions with seeded
+                     orthogonal polarisations (seed 2312063670), sigma 1, t0 8, dt 0.05, 2000 steps;
+                     BF16x3 tensor-core history.
+  ellipsoid12288     octasphere level 5 scaled to semi-axes (2, 1, 0.5) (8192 tri / 12288 edges),
+                     dt 0.1, 1500 steps, GMRES tol 1e-8 (learned initial guess).
+  batch32            32 seeded scatterers (spheres, ellipsoids, tori) of 480..12288 edges, dt 0.2,
+                     1000 steps, one direction each.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import excitation, meshes
+
+
+def sphere480_fp64():
+    V, F = meshes.icosphere(2)
+    return dict(name="sphere480_fp64", V=V, F=F, dt=0.2, Nt=300, alpha=1.0,
+                pw=excitation.single(t0=8.0, sigma=2.0), precision="fp64")
+
+
+def torus864_fp32():
+    V, F = meshes.torus(1.0, 0.4, 24, 12)
+    return dict(name="torus864_fp32", V=V, F=F, dt=2.0, Nt=1000, alpha=1.0,
+                pw=excitation.single(t0=8.0, sigma=2.0), precision="fp32")
+
+
+def sphere7680_r64(n_dir: int = 64):
+    V, F = meshes.icosphere(4)
+    return dict(name="sphere7680_r64", V=V, F=F, dt=0.05, Nt=2000, alpha=1.0,
+                pw=excitation.fibonacci_batch(n_dir, seed=2312063670, t0=8.0, sigma=1.0),
+                precision="bf16x3")
+
+
+def ellipsoid12288():
+    V, F = meshes.ellipsoid(5, (2.0, 1.0, 0.5))
+    return dict(name="ellipsoid12288", V=V, F=F, dt=0.1, Nt=1500, alpha=1.0,
+                pw=excitation.single(t0=8.0, sigma=2.0), precision="fp32", solver="gmres",
+                gmres_tol=1e-8)
+
+
+def batch32(seed: int = 2312063675, n: int = 32):
+    """32 seeded scatterers from size menus (edges 480..12288)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    probs = []
+    for s in range(n):
+        fam = int(rng.integers(0, 3))
+        if fam == 0:
+            lvl = int(rng.integers(2, 5))              # icosphere 480 / 1920 / 7680 edges
+            V, F = meshes.icosphere(lvl)
+        elif fam == 1:
+            lvl = int(rng.integers(3, 6))              # octasphere 768 / 3072 / 12288 edges
+            ax = rng.uniform(0.5, 2.0, size=3)
+            V, F = meshes.ellipsoid(lvl, tuple(ax))
+        else:
+            nv = int(rng.choice([8, 12, 16, 24, 32]))
+            nu = int(rng.choice([2, 4])) * nv
+            rr = float(rng.uniform(0.2, 0.5))
+            V, F = meshes.torus(1.0, rr, nu, nv)
+        pw = excitation.random_batch(1, seed=seed + 1000 + s, t0=8.0, sigma=2.0)
+        probs.append(dict(name=f"batch32_{s}", V=V, F=F, dt=0.2, Nt=1000, alpha=1.0, pw=pw,
+                          precision="fp32"))
+    return probs
+
+
+def small_sphere(level: int = 1, dt: float = 0.4, Nt: int = 40):
+    """Small icosphere case the oracle finishes in seconds (80 tri / 120 edges at level 1)."""
+    V, F = meshes.icosphere(level)
+    return dict(name=f"icosphere{level}", V=V, F=F, dt=dt, Nt=Nt, alpha=1.0,
+                pw=excitation.single(t0=8.0, sigma=2.0), precision="fp64")
+
+
+def small_torus(nu: int = 8, nv: int = 4, dt: float = 0.5, Nt: int = 40):
+    V, F = meshes.torus(1.0, 0.4, nu, nv)
+    return dict(name=f"torus{nu}x{nv}", V=V, F=F, dt=dt, Nt=Nt, alpha=1.0,
+                pw=excitation.single(t0=8.0, sigma=2.0), precision="fp64")
