@@ -1,0 +1,149 @@
+/*
+ * tdcfie.h -- C ABI of the GB300 (sm_103a) marching-on-in-time solver for the quasi-Helmholtz
+ * projected, Yukawa-Calderon preconditioned time-domain combined field integral equation
+ * (Le, Cordel, Andriulli, Cools, "A Stabilized Time-Domain Combined Field Integral Equation Using
+ * the Quasi-Helmholtz Projectors", arXiv 2312.06367).
+ *
+ * Natural units: c = eta = 1 (so kappa = 1/dt and T0 = D).  All entry points return a
+ * tdcfie_status (0 = success, negative = error) and never abort; tdcfie_last_error() gives a
+ * one-line message.  Handles are not thread-safe; every device operation of a handle runs on
+ * opts.stream.  Host arrays passed in are copied; device arrays passed in are used in place and
+ * remain owned by the caller.
+ */
+#ifndef TDCFIE_H
+#define TDCFIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tdcfie_s* tdcfie_t;
+
+typedef enum {
+    TDCFIE_OK = 0,
+    TDCFIE_E_ARG = -1,         /* invalid argument (null pointer, size <= 0, dt <= 0, ...) */
+    TDCFIE_E_MESH = -2,        /* mesh not closed / not manifold / inconsistently oriented / disconnected */
+    TDCFIE_E_OOM = -3,         /* device or host allocation failed */
+    TDCFIE_E_CUDA = -4,        /* a CUDA runtime call failed (message holds the CUDA error string) */
+    TDCFIE_E_NOCONV = -5,      /* GMRES did not reach the tolerance (step index in the message) */
+    TDCFIE_E_TIMEOUT = -6,     /* a bounded device-side wait ran out */
+    TDCFIE_E_NONFINITE = -7,   /* a NaN/Inf was produced (step index in the message) */
+    TDCFIE_E_STATE = -8,       /* call out of order (e.g. march before assemble) */
+    TDCFIE_E_UNSUPPORTED = -9  /* option combination not built (e.g. BF16X3 with R not a multiple of 16) */
+} tdcfie_status;
+
+/* Arithmetic of the per-step history sum and solve (Sec. IV-B).  FP64: everything FP64.
+ * FP32: FP32 matrices and vectors, FP32 accumulation.  BF16X3: matrices and vectors split into
+ * bf16 hi + lo, three tensor-core products (hi*hi + hi*lo + lo*hi) with FP32 accumulation. */
+typedef enum { TDCFIE_FP64 = 0, TDCFIE_FP32 = 1, TDCFIE_BF16X3 = 2 } tdcfie_precision;
+/* Solve with T_0 each step: DIRECT = explicit FP64-factored inverse applied in path precision;
+ * GMRES = restarted GMRES on T_0 (path-precision matvec, FP64 residual and orthogonalisation). */
+typedef enum { TDCFIE_SOLVE_DIRECT = 0, TDCFIE_SOLVE_GMRES = 1 } tdcfie_solver;
+typedef enum { TDCFIE_GUESS_ZERO = 0, TDCFIE_GUESS_PREV = 1, TDCFIE_GUESS_MLP = 2 } tdcfie_guess;
+
+typedef struct {
+    int precision;        /* tdcfie_precision, default TDCFIE_FP64 */
+    int solver;           /* tdcfie_solver, default TDCFIE_SOLVE_DIRECT */
+    double gmres_tol;     /* relative FP64 residual target, default 1e-8 */
+    int gmres_restart;    /* Krylov dimension per cycle, default 30 */
+    int gmres_maxit;      /* total iteration cap per step, default 300 */
+    int guess;            /* tdcfie_guess for GMRES, default TDCFIE_GUESS_PREV */
+    int64_t max_rhs;      /* R: right-hand sides (incident waves) marched together, default 1 */
+    void* stream;         /* cudaStream_t; NULL = the legacy default stream */
+    int device;           /* CUDA device ordinal, default 0 */
+} tdcfie_opts;
+
+/* Fill *opts with the defaults above. */
+void tdcfie_default_opts(tdcfie_opts* opts);
+
+/*
+ * Create a solver for the closed, connected, orientable triangulated surface Gamma (Sec. II-A):
+ *   vertices  host, nv x 3 float64, row-major;
+ *   triangles host, nc x 3 int32 vertex indices, counter-clockwise about the outward normal.
+ * dt: time step (> 0); nt: steps a march produces; alpha: coupling of the MFIE part (the
+ * paper's eta^2 in Eq. qHP_TDCFIE; 1 in natural units).
+ * Builds the edge table (edges = sorted unique vertex pairs, oriented min -> max), the
+ * incidence matrices Lambda and Sigma (Sec. II-D), the barycentric refinement and the BC table
+ * (Sec. II-C), D (largest vertex distance), T0 = D, and the number of time blocks
+ * K = ceil(D/dt + 2).  Host work only (no device is touched until tdcfie_assemble, which
+ * uploads the tables).  *out receives the handle.
+ * Errors: TDCFIE_E_ARG, TDCFIE_E_MESH, TDCFIE_E_OOM, TDCFIE_E_CUDA.
+ */
+tdcfie_status tdcfie_create(const double* vertices, int64_t nv, const int32_t* triangles, int64_t nc,
+                            double dt, int64_t nt, double alpha, const tdcfie_opts* opts, tdcfie_t* out);
+
+/*
+ * Assemble on the device (FP64): retarded matrices S_k, H_k, MM_k (Sec. II-C, IV-A), the static
+ * Yukawa matrices Z^s, Z^h, M and the Gram matrix G (Sec. II-B, II-C), the projectors
+ * (Sec. II-D), L1 = Z~ G^-T and L2 = X~ G^-1 (Sec. III), the dense blocks
+ * T_k = L1 ZZ~_k + alpha L2 XX~_k of Eq. dis_TD_CFIE, the inverse of T_0, and their copies in
+ * the path precision.  One-time; not part of a step.
+ */
+tdcfie_status tdcfie_assemble(tdcfie_t h);
+
+/* Plane waves e_in = amp p exp(-((t - k.r - t0)/width)^2), h_in = k x e_in (Sec. V, natural
+ * units).  Host arrays: k_hat R x 3 (unit), pol R x 3 (unit, orthogonal to k), amp, t0, width R. */
+typedef struct {
+    int64_t R;
+    const double* k_hat;
+    const double* pol;
+    const double* amp;
+    const double* t0;
+    const double* width;
+} tdcfie_plane_waves;
+
+/* Copy the excitation to the device (R must equal opts.max_rhs) and reset the march to n = 0
+ * (history cleared: y_i = 0 for i <= 0, causality of Sec. II-A). */
+tdcfie_status tdcfie_set_excitation(tdcfie_t h, const tdcfie_plane_waves* exc);
+
+/*
+ * Advance the march by nsteps steps of the MOT recurrence (Sec. IV-B):
+ *   r_n = -L1 (dtt P^LH + P^S) e(t_n) + alpha L2 h(t_n)
+ *   y_n = T_0^-1 (r_n - sum_{k=1}^{K-1} T_k y_{n-k})
+ *   j_n = P^LH y_n + P^S (y_n - y_{n-1}) / dtt          (Eq. post_processing)
+ * currents_out: DEVICE buffer of nsteps x R x N_E elements (step-major, then incident wave, then
+ * edge), float64 for TDCFIE_FP64 and float32 otherwise; may be NULL to discard the currents.
+ * The march state (step counter, ring of the last K-1 y, the last y) persists across calls.
+ */
+tdcfie_status tdcfie_step(tdcfie_t h, int64_t nsteps, void* currents_out);
+
+/* Whole march: set_excitation, then nt steps into currents_out.  out_on_host != 0: currents_out is a
+ * HOST buffer (pinned or pageable) and the device-to-host copy is part of the call. */
+tdcfie_status tdcfie_march(tdcfie_t h, const tdcfie_plane_waves* exc, void* currents_out, int out_on_host);
+
+/* Sizes of the discretisation. Any pointer may be NULL. */
+tdcfie_status tdcfie_info(tdcfie_t h, int64_t* ne, int64_t* nc, int64_t* nv, int64_t* K, int32_t* genus,
+                          double* D);
+
+/* Edge table for bit-exact checks: edges ne x 2 (v-, v+), cplus / cminus ne (host outputs). */
+tdcfie_status tdcfie_topology(tdcfie_t h, int32_t* edges, int32_t* cplus, int32_t* cminus);
+
+/* BC coefficient table of the barycentric refinement (Sec. II-C, Fig. 2), host outputs:
+ * nentries; per entry the fine triangle, the BC function (edge) and the three outward fluxes
+ * through the fine triangle's edges opposite its vertices 0, 1, 2 (g_n = sum_j phi_j (r - w_j)/(2A));
+ * fine_vertices (nv + ne + nc) x 3 (vertices, edge midpoints, barycentres); fine_triangles
+ * (6 nc) x 3.  Any output may be NULL (query nentries first). */
+tdcfie_status tdcfie_bc_table(tdcfie_t h, int64_t* nentries, int32_t* fine_tri, int32_t* fn, double* phi,
+                              double* fine_vertices, int32_t* fine_triangles);
+
+/* Copy an assembled FP64 matrix to a host buffer (row-major):
+ *   which 0: T_k (ne x ne), 1: S_k (ne x ne), 2: H_k (ne x ne), 3: MM_k (ne x ne),
+ *   4: G, 5: Z^s, 6: Z^h, 7: M, 8: P^Sigma, 9: L1, 10: L2 (ne x ne; k ignored). */
+tdcfie_status tdcfie_get_matrix(tdcfie_t h, int which, int64_t k, double* host_out);
+
+/* Device time (ms, CUDA events on the handle's stream) of the last tdcfie_step call and of its
+ * history-sum kernels alone; history_bytes = algorithmic bytes those kernels stream per step. */
+tdcfie_status tdcfie_last_timing(tdcfie_t h, double* step_ms, double* history_ms, double* history_bytes,
+                                 int64_t* kernel_launches);
+
+tdcfie_status tdcfie_destroy(tdcfie_t h);
+
+/* Message of the last error of h (thread-local last error when h is NULL). Never NULL. */
+const char* tdcfie_last_error(tdcfie_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDCFIE_H */

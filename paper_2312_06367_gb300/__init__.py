@@ -1,0 +1,125 @@
+"""GB300 (sm_103a) marching-on-in-time solver for the quasi-Helmholtz projected TD-CFIE.
+
+Thin Python layer over the C ABI in include/tdcfie.h (libtdcfie.so, built in-tree).  PyTorch is
+used only for device memory and streams; every step of the march runs in the library's CUDA
+kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import BF16X3, FP32, FP64, TdcfieError  # noqa: F401
+
+__all__ = ["Solver", "FP64", "FP32", "BF16X3", "TdcfieError"]
+
+_PREC = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
+
+
+class Solver:
+    """One scatterer: create (host tables) -> assemble (device, FP64) -> march/step (hot path)."""
+
+    def __init__(self, V, F, dt: float, nt: int, alpha: float = 1.0, precision="fp64", R: int = 1,
+                 stream=None, device: int = 0):
+        L = _lib.load()
+        self._V = np.ascontiguousarray(V, dtype=np.float64)
+        self._F = np.ascontiguousarray(F, dtype=np.int32)
+        o = _lib.default_opts()
+        o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+        o.max_rhs = int(R)
+        o.device = int(device)
+        o.stream = ctypes.c_void_p(stream) if stream else None
+        self.precision = o.precision
+        self.R = int(R)
+        self.nt = int(nt)
+        h = ctypes.c_void_p()
+        _lib.check(L.tdcfie_create(_lib._ptr(self._V), self._V.shape[0], _lib._ptr(self._F), self._F.shape[0],
+                                   float(dt), int(nt), float(alpha), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        ne, nc, nv, K = (ctypes.c_int64() for _ in range(4))
+        g = ctypes.c_int32()
+        D = ctypes.c_double()
+        _lib.check(L.tdcfie_info(h, ctypes.byref(ne), ctypes.byref(nc), ctypes.byref(nv), ctypes.byref(K),
+                                 ctypes.byref(g), ctypes.byref(D)), h)
+        self.ne, self.nc, self.nv, self.K, self.genus, self.D = ne.value, nc.value, nv.value, K.value, g.value, D.value
+
+    # ------------------------------------------------------------------ host queries
+    def topology(self):
+        E = np.zeros((self.ne, 2), dtype=np.int32)
+        cp = np.zeros(self.ne, dtype=np.int32)
+        cm = np.zeros(self.ne, dtype=np.int32)
+        _lib.check(_lib.load().tdcfie_topology(self._h, _lib._ptr(E), _lib._ptr(cp), _lib._ptr(cm)), self._h)
+        return E, cp, cm
+
+    def bc_table(self):
+        L = _lib.load()
+        n = ctypes.c_int64()
+        _lib.check(L.tdcfie_bc_table(self._h, ctypes.byref(n), None, None, None, None, None), self._h)
+        ft = np.zeros(n.value, dtype=np.int32)
+        fn = np.zeros(n.value, dtype=np.int32)
+        ph = np.zeros((n.value, 3), dtype=np.float64)
+        fV = np.zeros((self.nv + self.ne + self.nc, 3), dtype=np.float64)
+        fF = np.zeros((6 * self.nc, 3), dtype=np.int32)
+        _lib.check(L.tdcfie_bc_table(self._h, ctypes.byref(n), _lib._ptr(ft), _lib._ptr(fn), _lib._ptr(ph),
+                                     _lib._ptr(fV), _lib._ptr(fF)), self._h)
+        return ft, fn, ph, fV, fF
+
+    # ------------------------------------------------------------------ device work
+    def assemble(self):
+        _lib.check(_lib.load().tdcfie_assemble(self._h), self._h)
+        return self
+
+    def matrix(self, which: str, k: int = 0) -> np.ndarray:
+        ids = {"T": 0, "S": 1, "H": 2, "MM": 3, "G": 4, "Zs": 5, "Zh": 6, "M": 7, "PS": 8, "L1": 9, "L2": 10}
+        out = np.zeros((self.ne, self.ne), dtype=np.float64)
+        _lib.check(_lib.load().tdcfie_get_matrix(self._h, ids[which], int(k), _lib._ptr(out)), self._h)
+        return out
+
+    def _pw(self, pw: dict):
+        arrs = [np.ascontiguousarray(pw[k], dtype=np.float64) for k in ("k", "p", "amp", "t0", "sigma")]
+        self._pw_keep = arrs
+        return _lib.PlaneWaves(arrs[0].shape[0], *(a.ctypes.data for a in arrs))
+
+    def set_excitation(self, pw: dict):
+        p = self._pw(pw)
+        _lib.check(_lib.load().tdcfie_set_excitation(self._h, ctypes.byref(p)), self._h)
+
+    def step(self, nsteps: int, out=None):
+        """out: torch CUDA tensor (nsteps, R, ne) of the path dtype, or None to discard."""
+        ptr = None if out is None else ctypes.c_void_p(out.data_ptr())
+        _lib.check(_lib.load().tdcfie_step(self._h, int(nsteps), ptr), self._h)
+
+    def march(self, pw: dict, out=None, out_on_host: bool = False):
+        p = self._pw(pw)
+        if out is None:
+            ptr = None
+        elif isinstance(out, np.ndarray):
+            ptr = _lib._ptr(out)
+        else:
+            ptr = ctypes.c_void_p(out.data_ptr())
+        _lib.check(_lib.load().tdcfie_march(self._h, ctypes.byref(p), ptr, int(out_on_host)), self._h)
+
+    def timing(self):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64()
+        _lib.check(_lib.load().tdcfie_last_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                                  ctypes.byref(n)), self._h)
+        return {"step_ms": a.value, "history_ms": b.value, "history_bytes": c.value, "launches": n.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().tdcfie_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.precision == FP64 else torch.float32
