@@ -25,6 +25,14 @@
  *     edge, and into pieces of width <= 1; radial variable u = asinh(rho / |d|)
  *     (rho itself when d = 0), split at the breakpoint radii and into pieces of width
  *     <= 1.  NANG Gauss-Legendre points per angular piece, NRAD per radial piece.
+ *   retarded pairs (other than a triangle with itself) whose projection point p is well outside the
+ *     source triangle (every vertex at least two longest edges from p): the same polar coordinates,
+ *     but the angle runs over the triangle's own
+ *     angular range seen from p, in two halves split at the middle vertex; in each half the
+ *     angular variable is psi = asinh(tan(theta - theta_f)) along the nearer boundary edge
+ *     (theta_f: its foot direction), split where breakpoint circles cross either boundary edge
+ *     and into pieces of width <= 1; the radius runs from the near edge to the far edge (split at
+ *     the breakpoint radii, u-variable pieces of width <= 1); no signed cancellation.
  *   static far pairs (parents share no vertex): product rules (3 x 3 fine-fine,
  *     3 x 7 fine-coarse).
  *   coplanar pairs (same coarse parent): the curl kernel vanishes identically
@@ -72,6 +80,8 @@ static inline void cross3(const double* a, const double* b, double* o) {
 static inline double norm3(const double* a) { return sqrt(dot3(a, a)); }
 
 typedef void (*point_cb)(void* ctx, double R, double W, const double* ymx);
+static int share_vertex(const int* F, int a, int b);
+
 
 /* Integrate a function of y over the triangle (v0, v1, v2) for the outer point x:
    calls cb(ctx, R, W, y - x) at every inner node; the sum of W*G(y) approximates the
@@ -177,6 +187,157 @@ static void polar_rule(const double* x, const double* v0, const double* v1, cons
     }
 }
 
+
+/* 2-D cross product */
+static inline double cr2(double ax, double ay, double bx, double by) { return ax * by - ay * bx; }
+
+/* Far-pair rule: integrate over the triangle only, in polar coordinates about p (projection of x),
+   when p lies outside the triangle; otherwise the sub-triangle rule above (all signs positive). */
+static void polar_far(const double* x, const double* v0, const double* v1, const double* v2,
+                      const double* brk, int nbrk, point_cb cb, void* ctx) {
+    double e1[3], e2[3], n[3], tmp[3];
+    sub3(v1, v0, e1); sub3(v2, v0, e2); cross3(e1, e2, n);
+    double nn = norm3(n);
+    n[0] /= nn; n[1] /= nn; n[2] /= nn;
+    sub3(x, v0, tmp);
+    double d = dot3(tmp, n);
+    double ad = fabs(d);
+    double p[3] = {x[0] - d * n[0], x[1] - d * n[1], x[2] - d * n[2]};
+    const double* V[3] = {v0, v1, v2};
+    /* inside test: signed areas of (p, v_i, v_{i+1}) all >= 0 */
+    int inside = 1;
+    for (int i = 0; i < 3; ++i) {
+        double a[3], b[3], c[3];
+        sub3(V[i], p, a); sub3(V[(i + 1) % 3], p, b); cross3(a, b, c);
+        if (dot3(c, n) < 0.0) inside = 0;
+    }
+    /* the far form only when p is well outside: every vertex at least two longest edges away */
+    double lmax = 0.0, vmin = 1e300;
+    for (int i = 0; i < 3; ++i) {
+        double a[3], b[3];
+        sub3(V[(i + 1) % 3], V[i], a);
+        lmax = fmax(lmax, norm3(a));
+        sub3(V[i], p, b);
+        vmin = fmin(vmin, norm3(b));
+    }
+    if (inside || vmin < 2.0 * lmax) { polar_rule(x, v0, v1, v2, brk, nbrk, 0, cb, ctx); return; }
+    /* in-plane frame: u toward the centroid, w = n x u */
+    double g[3] = {(v0[0] + v1[0] + v2[0]) / 3.0 - p[0], (v0[1] + v1[1] + v2[1]) / 3.0 - p[1], (v0[2] + v1[2] + v2[2]) / 3.0 - p[2]};
+    double gl = norm3(g);
+    double u[3] = {g[0] / gl, g[1] / gl, g[2] / gl}, w[3];
+    cross3(n, u, w);
+    double X[3], Y[3], ph[3];
+    for (int i = 0; i < 3; ++i) {
+        double a[3];
+        sub3(V[i], p, a);
+        X[i] = dot3(a, u); Y[i] = dot3(a, w);
+        ph[i] = atan2(Y[i], X[i]);
+    }
+    int o[3] = {0, 1, 2};
+    for (int i = 1; i < 3; ++i) { int t = o[i], j = i - 1; while (j >= 0 && ph[o[j]] > ph[t]) { o[j + 1] = o[j]; --j; } o[j + 1] = t; }
+    const int L = o[0], Mv = o[1], H = o[2];
+    double rb[MAXBRK]; int nrb = 0;
+    for (int b = 0; b < nbrk; ++b) if (brk[b] > ad) rb[nrb++] = sqrt(brk[b] * brk[b] - d * d);
+    /* two angular halves: [phi_L, phi_M] bounded by edges LH and LM, [phi_M, phi_H] by LH and MH */
+    for (int half = 0; half < 2; ++half) {
+        const double P0 = half == 0 ? ph[L] : ph[Mv], P1 = half == 0 ? ph[Mv] : ph[H];
+        if (!(P1 > P0)) continue;
+        const int ea[2] = {L, half == 0 ? L : Mv}, eb[2] = {H, half == 0 ? Mv : H};
+        /* near edge: the one the mid-angle ray meets first */
+        double re_mid[2];
+        {
+            const double th = 0.5 * (P0 + P1), c = cos(th), sn = sin(th);
+            for (int ei = 0; ei < 2; ++ei) {
+                const double ax = X[ea[ei]], ay = Y[ea[ei]], bx = X[eb[ei]], by = Y[eb[ei]];
+                re_mid[ei] = cr2(ax, ay, bx - ax, by - ay) / cr2(c, sn, bx - ax, by - ay);
+            }
+        }
+        const int en = re_mid[0] < re_mid[1] ? 0 : 1;
+        /* foot of the perpendicular from p on the near edge line: distance hn, angle thf */
+        const double nax = X[ea[en]], nay = Y[ea[en]], nbx = X[eb[en]], nby = Y[eb[en]];
+        const double ndx = nbx - nax, ndy = nby - nay, nl2 = ndx * ndx + ndy * ndy;
+        const double tf = -(nax * ndx + nay * ndy) / nl2;
+        const double fx = nax + tf * ndx, fy = nay + tf * ndy;
+        const double hn = sqrt(fx * fx + fy * fy);
+        if (!(hn > 0.0)) continue;
+        const double thf = atan2(fy, fx);
+        /* split angles: crossings of the breakpoint circles with both boundary edges */
+        double sp[2 * 2 * MAXBRK + 2]; int nsp = 0;
+        sp[nsp++] = P0;
+        for (int ei = 0; ei < 2; ++ei) {
+            const double ax = X[ea[ei]], ay = Y[ea[ei]], bx = X[eb[ei]], by = Y[eb[ei]];
+            const double dx = bx - ax, dy = by - ay, dd = dx * dx + dy * dy;
+            for (int q = 0; q < nrb; ++q) {
+                const double bq = ax * dx + ay * dy, cq = ax * ax + ay * ay - rb[q] * rb[q];
+                const double disc = bq * bq - dd * cq;
+                if (disc <= 0.0) continue;
+                const double sq = sqrt(disc);
+                const double ts[2] = {(-bq - sq) / dd, (-bq + sq) / dd};
+                for (int k = 0; k < 2; ++k) {
+                    if (ts[k] <= 0.0 || ts[k] >= 1.0) continue;
+                    const double ang = atan2(ay + ts[k] * dy, ax + ts[k] * dx);
+                    if (ang > P0 && ang < P1) sp[nsp++] = ang;
+                }
+            }
+        }
+        sp[nsp++] = P1;
+        for (int i = 1; i < nsp; ++i) { double v = sp[i]; int j = i - 1; while (j >= 0 && sp[j] > v) { sp[j + 1] = sp[j]; --j; } sp[j + 1] = v; }
+        /* angular variable psi = asinh(tan(theta - thf)) along the near edge; d theta = d psi / cosh psi */
+        for (int piece = 0; piece + 1 < nsp; ++piece) {
+            const double S0 = asinh(tan(sp[piece] - thf)), S1 = asinh(tan(sp[piece + 1] - thf));
+            if (!(S1 > S0)) continue;
+            int nsub = (int)ceil((S1 - S0) / PIECE);
+            if (nsub < 1) nsub = 1;
+            const double hw = (S1 - S0) / nsub;
+            for (int sb = 0; sb < nsub; ++sb) {
+                for (int ga = 0; ga < NANG; ++ga) {
+                    const double psi = S0 + sb * hw + 0.5 * hw * (GA_X[ga] + 1.0);
+                    const double wth = 0.5 * hw * GA_W[ga] / cosh(psi);
+                    const double th = thf + atan(sinh(psi));
+                    const double c = cos(th), sn = sin(th);
+                    double re[2];
+                    for (int ei = 0; ei < 2; ++ei) {
+                        const double ax = X[ea[ei]], ay = Y[ea[ei]], bx = X[eb[ei]], by = Y[eb[ei]];
+                        re[ei] = cr2(ax, ay, bx - ax, by - ay) / cr2(c, sn, bx - ax, by - ay);
+                    }
+                    const double r0 = re[en], r1 = re[1 - en];
+                    double om[3] = {c * u[0] + sn * w[0], c * u[1] + sn * w[1], c * u[2] + sn * w[2]};
+                    double rp[MAXBRK + 2]; int nrp = 0;
+                    rp[nrp++] = r0;
+                    for (int q = 0; q < nrb; ++q) if (rb[q] > r0 && rb[q] < r1) rp[nrp++] = rb[q];
+                    rp[nrp++] = r1;
+                    for (int i = 1; i < nrp; ++i) { double v = rp[i]; int j = i - 1; while (j >= 0 && rp[j] > v) { rp[j + 1] = rp[j]; --j; } rp[j + 1] = v; }
+                    for (int ri = 0; ri + 1 < nrp; ++ri) {
+                        const double a0 = rp[ri], a1 = rp[ri + 1];
+                        if (!(a1 > a0)) continue;
+                        if (ad > 0.0) {
+                            const double u0 = asinh(a0 / ad), u1 = asinh(a1 / ad);
+                            int ns = (int)ceil((u1 - u0) / PIECE);
+                            if (ns < 1) ns = 1;
+                            const double uw = (u1 - u0) / ns;
+                            for (int k = 0; k < ns; ++k)
+                                for (int gr = 0; gr < NRAD; ++gr) {
+                                    const double uu = u0 + k * uw + 0.5 * uw * (GR_X[gr] + 1.0);
+                                    const double rho = ad * sinh(uu), R = ad * cosh(uu);
+                                    const double W = wth * 0.5 * uw * GR_W[gr] * rho * R;
+                                    double ymx[3] = {rho * om[0] - d * n[0], rho * om[1] - d * n[1], rho * om[2] - d * n[2]};
+                                    cb(ctx, R, W, ymx);
+                                }
+                        } else {
+                            const double rw = a1 - a0;
+                            for (int gr = 0; gr < NRAD; ++gr) {
+                                const double rho = a0 + 0.5 * rw * (GR_X[gr] + 1.0);
+                                double ymx[3] = {rho * om[0], rho * om[1], rho * om[2]};
+                                cb(ctx, rho, wth * 0.5 * rw * GR_W[gr] * rho, ymx);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 /* ---------------- temporal basis (Sec. IV-A) ---------------- */
 static double h0(double t, double dt) {
     if (t >= -dt && t < 0.0) return 1.0 + t / dt;
@@ -219,12 +380,14 @@ static void test_cb(void* c, double R, double W, const double* ymx) {
     t->m0 += W * F;
     for (int i = 0; i < 3; ++i) t->m1[i] += W * F * ymx[i];
 }
-/* out: m0, m1[3] (moment about x).  kind 0: 1, 1: 1/R, 2: exp(-p1 R)/R, 3: 1/R^3,
+/* out: m0, m1[3] (moment about x).  coplanar: 0 general, 1 coplanar (d = 0), 2 far-pair rule.
+   kind 0: 1, 1: 1/R, 2: exp(-p1 R)/R, 3: 1/R^3,
    4: q0(p1 - R)/R, 5: h0dot(p1 - R)/R, 6: h0(p1 - R)/R^3 (p2 = dt). */
 void oq_triangle_moments(const double* x, const double* v0, const double* v1, const double* v2,
                          const double* brk, int nbrk, int coplanar, int kind, double p1, double p2, double* out) {
     test_ctx t = {kind, p1, p2, 0.0, {0, 0, 0}};
-    polar_rule(x, v0, v1, v2, brk, nbrk, coplanar, test_cb, &t);
+    if (coplanar == 2) polar_far(x, v0, v1, v2, brk, nbrk, test_cb, &t);   /* far-pair rule */
+    else polar_rule(x, v0, v1, v2, brk, nbrk, coplanar, test_cb, &t);
     out[0] = t.m0; out[1] = t.m1[0]; out[2] = t.m1[1]; out[3] = t.m1[2];
 }
 
@@ -300,7 +463,8 @@ void oq_retarded_efie(const double* Vx, int nc, const int* F, int ne, const int*
                 double A2 = tri_area(v[0], v[1], v[2], NULL);
                 memset(s0, 0, sizeof(double) * K); memset(s1, 0, sizeof(double) * 3 * K); memset(p0, 0, sizeof(double) * K);
                 ret_ctx r = {K, dt, T0, s0, s1, p0, NULL, NULL, 1, 0};
-                polar_rule(x, v[0], v[1], v[2], brk, nb, c2 == c, ret_cb, &r);
+                if (c2 == c) polar_rule(x, v[0], v[1], v[2], brk, nb, 1, ret_cb, &r);
+                else polar_far(x, v[0], v[1], v[2], brk, nb, ret_cb, &r);
                 for (int k = 0; k < K; ++k) {
                     rowP[(size_t)k * nc + c2] += wx * p0[k] / (A * A2);
                     if (s0[k] == 0.0 && s1[3 * k] == 0.0 && s1[3 * k + 1] == 0.0 && s1[3 * k + 2] == 0.0) continue;
@@ -361,7 +525,7 @@ void oq_retarded_mfie(const double* Vx, int nc, const int* F, int ne, const int*
                 double A2 = tri_area(v[0], v[1], v[2], NULL);
                 memset(m0, 0, sizeof(double) * K); memset(m1, 0, sizeof(double) * 3 * K);
                 ret_ctx r = {K, dt, 0.0, NULL, NULL, NULL, m0, m1, 0, 1};
-                polar_rule(x, v[0], v[1], v[2], brk, nb, 0, ret_cb, &r);
+                polar_far(x, v[0], v[1], v[2], brk, nb, ret_cb, &r);
                 for (int k = 0; k < K; ++k) {
                     if (m0[k] == 0.0 && m1[3 * k] == 0.0 && m1[3 * k + 1] == 0.0 && m1[3 * k + 2] == 0.0) continue;
                     for (int j = 0; j < 3; ++j) {

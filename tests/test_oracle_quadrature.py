@@ -120,6 +120,36 @@ def test_retarded_kernels_with_breakpoints(x, kind):
     assert abs(m0 - ref) < 1e-8 * max(1e-3, abs(ref)), (m0, ref)
 
 
+# every vertex of TRI at least two longest edges (2.28) from the projection: the far form applies
+FAR_POINTS = [[3.0, -2.0, 1.0], [4.0, 3.5, 0.4], [-3.0, 0.4, 0.8], [0.5, -3.2, 0.05], [3.5, 3.0, 0.3]]
+
+
+@pytest.mark.parametrize("x", FAR_POINTS)
+def test_far_rule_closed_forms(x):
+    """The far-pair rule (angle over the triangle's own range, no signed cancellation)."""
+    x = np.array(x)
+    m0, _ = cquad.triangle_moments(x, *TRI, kind=1, coplanar=2)
+    ref = potential_closed_form(x, TRI)
+    assert abs(m0 - ref) < 1e-9 * abs(ref)
+    m0, m1 = cquad.triangle_moments(x, *TRI, kind=3, coplanar=2)
+    om = solid_angle(x, TRI)
+    assert abs(m1[2] - om) < 1e-7 * abs(om)
+
+
+@pytest.mark.parametrize("x", [[3.2, 2.9, 0.3], [-2.5, -1.5, 0.2], [1.0, 3.5, 0.6]])
+@pytest.mark.parametrize("kind", [4, 5])
+def test_far_rule_with_breakpoints(x, kind):
+    x = np.array(x)
+    dt = 0.11
+    k = int(np.linalg.norm(x - np.array([0.4, 0.33, 0.0])) / dt) + 1
+    brk = [j * dt for j in range(1, 80)]
+    L = cquad.lib()
+    f = (lambda R: L.oq_q0(k * dt - R, dt)) if kind == 4 else (lambda R: L.oq_h0dot(k * dt - R, dt))
+    m0, _ = cquad.triangle_moments(x, *TRI, kind=kind, p1=k * dt, p2=dt, brk=brk, coplanar=2)
+    ref = _adaptive_retarded(x, TRI, f, brk)
+    assert abs(m0 - ref) < 1e-8 * max(1e-3, abs(ref)), (m0, ref)
+
+
 def test_rule_refinement_changes_matrices_little():
     from oracle.assemble import Operators
     from synth import meshes
