@@ -1,0 +1,329 @@
+"""Benchmark of the MOT hot path (one JSON line on rank 0).
+
+A step is one pass of the whole hot path for all right-hand sides of the workload: plane-wave
+tests, history sum with the right-hand-side blocks, T_0 solve, projector and post-processing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+N > 1 (torchrun): every rank marches its own copy of the workload (independent incident-wave
+batches; weak scaling, no data-path collective); value = all ranks' steps / max time.
+--impl reference times the FP64 CPU oracle (a deliberately slow reference program) on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "sphere7680_r64"
+L2_BYTES = 126 * 2 ** 20
+METRIC = "MOT steps/s"
+
+
+def workload(name: str, precision: str | None = None):
+    from synth import workloads
+    w = {
+        "sphere480_fp64": workloads.sphere480_fp64,
+        "torus864_fp32": workloads.torus864_fp32,
+        "sphere7680_r64": workloads.sphere7680_r64,
+        "sphere1920_r64": workloads.sphere1920_r64,
+    }[name]()
+    if precision:
+        w["precision"] = precision
+    if name == "torus864_fp32":
+        # alpha = 1 puts a real polynomial eigenvalue of modulus 1.89 outside the unit circle at
+        # this time step on this torus; alpha = 0.5 keeps the spectrum inside (radius 0.84)
+        w["alpha"] = 0.5
+    return w
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_dense_rate(w, steps: int = 3):
+    """Oracle dense march (oracle.mot.march_dense, FP64 numpy) on blocks of the workload's size.
+
+    For meshes whose FP64 oracle assembly takes hours, the timed sample is the oracle's own
+    marching step applied to dense FP64 blocks of the workload's size (N edges, K blocks, R
+    waves) filled with synthetic values; the arithmetic per step does not depend on the values."""
+    import numpy as np
+
+    from oracle import mot
+    from oracle.topology import Topology, n_lags
+    t = Topology(w["V"], w["F"])
+    K = n_lags(t.D, w["dt"])
+    R = int(w["pw"]["k"].shape[0])
+    T = np.empty((K, t.ne, t.ne))
+    rng = np.random.default_rng(0)
+    row = rng.standard_normal(t.ne) / t.ne
+    T[:] = row[None, None, :]
+    T[0] += 4.0 * np.eye(t.ne)
+    r = rng.standard_normal((K + steps, t.ne, R))
+    mot.march_dense(T, r[:2])              # warm-up (LU of T_0 and BLAS threads)
+    t1 = time.time()
+    mot.march_dense(T, r[: K + steps])
+    el = time.time() - t1
+    # the march of K + steps steps: the first K - 1 steps see fewer history blocks; count the
+    # block-matvec work and express the rate in full steps (K - 1 history blocks each)
+    full_equiv = sum(min(n, K - 1) for n in range(K + steps)) / (K - 1)
+    return full_equiv / el, K + steps, K
+
+
+def cpu_oracle_rate(w, max_steps: int, budget_s: float = 20.0):
+    """Oracle (FP64, numpy + plain C) march on the host cores: steps/s over a bounded sample."""
+    import numpy as np
+    if w["F"].shape[0] > 2000:
+        rate, n, K = cpu_oracle_dense_rate(w)
+        return rate, n, None
+    from oracle import mot, rhs
+    from oracle.assemble import Operators
+    from oracle.formulation import Formulation
+    t0 = time.time()
+    ops = Operators(w["V"], w["F"], dt=w["dt"], alpha=w["alpha"])
+    fm = Formulation(ops)
+    t_asm = time.time() - t0
+    # calibrate the sample so the march takes about budget_s
+    n = min(max_steps, w["Nt"])
+    e, h = rhs.incident_tests(ops, w["pw"], w["dt"] * np.arange(1, n + 1))
+    r = fm.rhs(e, h)
+    t1 = time.time()
+    mot.march_factored(fm, r[: min(n, 20)])
+    per = (time.time() - t1) / min(n, 20)
+    n = int(max(10, min(n, budget_s / max(per, 1e-6))))
+    t1 = time.time()
+    mot.march_factored(fm, r[:n])
+    dt = time.time() - t1
+    return n / dt, n, t_asm
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    rate, n, t_asm = cpu_oracle_rate(w, args.steps * 20, budget_s=min(60.0, 5.0 * args.steps))
+    cores = os.cpu_count()
+    sample = (f"{n} march steps after an untimed {t_asm:.1f} s assembly" if t_asm is not None else
+              f"oracle dense march, {n} steps on dense FP64 blocks of the workload's size (synthetic values; "
+              f"the FP64 oracle assembly of this mesh is out of reach), rate in full-history steps")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / rate, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["name"], "edges": int(w["F"].shape[0] * 3 // 2), "R": int(w["pw"]["k"].shape[0]),
+                   "dt": w["dt"], "alpha": w["alpha"]},
+        "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, w):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2312_06367_gb300 import Solver
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    R = int(w["pw"]["k"].shape[0])
+    prec = w["precision"]
+    t0 = time.time()
+    s = Solver(w["V"], w["F"], dt=w["dt"], nt=args.steps, alpha=w["alpha"], precision=prec, R=R,
+               stream=stream.cuda_stream, device=local).assemble()
+    t_asm = time.time() - t0
+    esz = 8 if prec == "fp64" else 4
+    work_bytes = s.timing()["history_bytes"]
+    flush = work_bytes < 2 * L2_BYTES
+    flush_buf = torch.empty(int(2 * L2_BYTES // 4), dtype=torch.float32, device=dev) if flush else None
+    out = torch.empty((args.steps, R, s.ne), dtype=s.dtype, device=dev)
+    s.set_excitation(w["pw"])
+
+    def barrier():
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            s.step(1)
+            if flush:
+                flush_buf.fill_(1.0)
+        barrier()
+        step_ms, hist_ms = [], []
+        with Clocks(local) as clk:
+            barrier()
+            wall0 = time.perf_counter()
+            if flush:
+                for i in range(args.steps):
+                    flush_buf.fill_(float(i))       # evict the L2 between timed steps
+                    s.step(1, out[i:i + 1])
+                    t = s.timing()
+                    step_ms.append(t["step_ms"])
+                    hist_ms.append(t["history_ms"])
+            else:
+                s.step(args.steps, out)
+                t = s.timing()
+                step_ms = [t["step_ms"]] * args.steps
+                hist_ms = [t["history_ms"]]
+            barrier()
+            wall1 = time.perf_counter()
+    dev_ms = sum(step_ms)
+    launches = s.timing()["launches"] if not flush else s.timing()["launches"] * args.steps
+    finite = bool(torch.isfinite(out).all().item())
+    # max over ranks
+    tot_ms = dev_ms
+    if pg:
+        t = torch.tensor([dev_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = ws * args.steps / (tot_ms / 1e3)
+    # end-to-end through the C ABI with host buffers: excitation from host, currents to pinned host
+    host_out = torch.empty((args.steps, R, s.ne), dtype=s.dtype, pin_memory=True).numpy()
+    barrier()
+    e0 = time.perf_counter()
+    s.march(w["pw"], host_out, out_on_host=True)
+    barrier()
+    e1 = time.perf_counter()
+    e2e = ws * args.steps / (e1 - e0)
+    # roofline of the dominant kernel (history sum: streams every history and right-hand-side block)
+    pk = peaks()
+    h_ms = statistics.mean(hist_ms) if hist_ms and hist_ms[0] > 0 else None
+    achieved = work_bytes / (h_ms / 1e3) / 1e9 if h_ms else None
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", f"history_{w['name']}.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3", "fp16x3": "fp16x3"}[prec],
+        "data": "synthetic",
+        "config": {"workload": w["name"], "edges": s.ne, "triangles": s.nc, "R": R, "K": s.K, "dt": w["dt"],
+                   "alpha": w["alpha"], "precision": prec,
+                   "cache": "L2 flushed between timed steps" if flush else "inputs larger than L2",
+                   "assemble_s": round(t_asm, 2), "wall_s": round(wall1 - wall0, 4), "finite": finite},
+        "e2e": {"value": e2e, "unit": "steps/s", "h2d_bytes_per_step": 88 * R / args.steps,
+                "d2h_bytes_per_step": R * s.ne * esz},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": (achieved / pk["hbm_gbs"]) if achieved else None, "traffic": traffic,
+                     "kernel": ("history sum (k_history + k_reduce)" if prec in ("fp64", "fp32") else
+                                "tcgen05 split-precision history GEMM (k_umma_bf16x3 + k_fixup)"),
+                     "algorithmic_bytes_per_launch": work_bytes,
+                     "peak_source": "measured" if not pk.get("fallback") else "fallback"},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, n, t_casm = cpu_oracle_rate(w, 4 * args.steps + 50)
+        sample = (f"{n} march steps of the same workload (assembly {t_casm:.1f} s untimed)" if t_casm is not None else
+                  f"oracle dense march, {n} steps on dense FP64 blocks of the workload's size (synthetic values; "
+                  f"the FP64 oracle assembly of this mesh is out of reach), rate in full-history steps")
+        line["cpu_baseline"] = {"value": rate, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    s.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=None, help="override the workload's path precision")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    w = workload(args.workload, args.precision)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

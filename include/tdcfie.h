@@ -35,9 +35,13 @@ typedef enum {
 } tdcfie_status;
 
 /* Arithmetic of the per-step history sum and solve (Sec. IV-B).  FP64: everything FP64.
- * FP32: FP32 matrices and vectors, FP32 accumulation.  BF16X3: matrices and vectors split into
- * bf16 hi + lo, three tensor-core products (hi*hi + hi*lo + lo*hi) with FP32 accumulation. */
-typedef enum { TDCFIE_FP64 = 0, TDCFIE_FP32 = 1, TDCFIE_BF16X3 = 2 } tdcfie_precision;
+ * FP32: FP32 matrices and vectors, FP32 accumulation (CUDA cores).  BF16X3: matrices and vectors
+ * split into bf16 hi + lo, three tensor-core products (hi*hi + hi*lo + lo*hi) with FP32
+ * accumulation.  FP16X3: the same with fp16 halves of power-of-two scaled values (per-row scales
+ * of every matrix block, one scale per vector slot and right-hand side), about 2^-22 instead of
+ * 2^-16 relative per stored entry at the same 4 bytes per entry.  BF16X3 and FP16X3 march exactly
+ * 64 right-hand sides; FP64 and FP32 at most 8. */
+typedef enum { TDCFIE_FP64 = 0, TDCFIE_FP32 = 1, TDCFIE_BF16X3 = 2, TDCFIE_FP16X3 = 3 } tdcfie_precision;
 /* Solve with T_0 each step: DIRECT = explicit FP64-factored inverse applied in path precision;
  * GMRES = restarted GMRES on T_0 (path-precision matvec, FP64 residual and orthogonalisation). */
 typedef enum { TDCFIE_SOLVE_DIRECT = 0, TDCFIE_SOLVE_GMRES = 1 } tdcfie_solver;
@@ -137,6 +141,11 @@ tdcfie_status tdcfie_get_matrix(tdcfie_t h, int which, int64_t k, double* host_o
  * history-sum kernels alone; history_bytes = algorithmic bytes those kernels stream per step. */
 tdcfie_status tdcfie_last_timing(tdcfie_t h, double* step_ms, double* history_ms, double* history_bytes,
                                  int64_t* kernel_launches);
+
+/* Wall-clock seconds of the phases of the last tdcfie_assemble (host output, 6 values): mesh upload,
+ * retarded EFIE quadrature, retarded MFIE quadrature, static quadrature, formation of the blocks
+ * (projectors, preconditioner, T_k, inverses), path-precision copies. */
+tdcfie_status tdcfie_assembly_timing(tdcfie_t h, double* seconds);
 
 tdcfie_status tdcfie_destroy(tdcfie_t h);
 

@@ -11,11 +11,11 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import BF16X3, FP32, FP64, TdcfieError  # noqa: F401
+from ._lib import BF16X3, FP16X3, FP32, FP64, TdcfieError  # noqa: F401
 
-__all__ = ["Solver", "FP64", "FP32", "BF16X3", "TdcfieError"]
+__all__ = ["Solver", "FP64", "FP32", "BF16X3", "FP16X3", "TdcfieError"]
 
-_PREC = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3}
+_PREC = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "fp16x3": FP16X3}
 
 
 class Solver:
@@ -107,6 +107,12 @@ class Solver:
         _lib.check(_lib.load().tdcfie_last_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                                   ctypes.byref(n)), self._h)
         return {"step_ms": a.value, "history_ms": b.value, "history_bytes": c.value, "launches": n.value}
+
+    def assembly_timing(self):
+        """Seconds per assembly phase: upload, retarded EFIE, retarded MFIE, static, formation, plan."""
+        out = np.zeros(6)
+        _lib.check(_lib.load().tdcfie_assembly_timing(self._h, _lib._ptr(out)), self._h)
+        return dict(zip(("upload", "retarded_efie", "retarded_mfie", "static", "formation", "plan"), out.tolist()))
 
     def close(self):
         if getattr(self, "_h", None):

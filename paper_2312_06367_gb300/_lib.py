@@ -12,7 +12,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtdcfie.so")
 
-FP64, FP32, BF16X3 = 0, 1, 2
+FP64, FP32, BF16X3, FP16X3 = 0, 1, 2, 3
 SOLVE_DIRECT, SOLVE_GMRES = 0, 1
 GUESS_ZERO, GUESS_PREV, GUESS_MLP = 0, 1, 2
 STATUS = {0: "OK", -1: "E_ARG", -2: "E_MESH", -3: "E_OOM", -4: "E_CUDA", -5: "E_NOCONV", -6: "E_TIMEOUT",
@@ -52,6 +52,7 @@ SIGNATURES = [
     ("tdcfie_bc_table", _I, [_P, _P, _P, _P, _P, _P, _P]),
     ("tdcfie_get_matrix", _I, [_P, _I, _I64, _P]),
     ("tdcfie_last_timing", _I, [_P, _P, _P, _P, _P]),
+    ("tdcfie_assembly_timing", _I, [_P, _P]),
     ("tdcfie_destroy", _I, [_P]),
     ("tdcfie_last_error", ctypes.c_char_p, [_P]),
 ]

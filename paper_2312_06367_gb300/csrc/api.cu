@@ -1,4 +1,5 @@
 // C ABI of the tdcfie library (include/tdcfie.h): argument checks, ownership, orchestration.
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -56,9 +57,12 @@ extern "C" tdcfie_status tdcfie_create(const double* vertices, int64_t nv, const
     tdcfie_opts o;
     tdcfie_default_opts(&o);
     if (opts) o = *opts;
-    if (o.precision < TDCFIE_FP64 || o.precision > TDCFIE_BF16X3) return fail(nullptr, TDCFIE_E_ARG, "bad precision");
+    if (o.precision < TDCFIE_FP64 || o.precision > TDCFIE_FP16X3) return fail(nullptr, TDCFIE_E_ARG, "bad precision");
+    const bool tensor = o.precision == TDCFIE_BF16X3 || o.precision == TDCFIE_FP16X3;
     if (o.max_rhs < 1 || o.max_rhs > 4096) return fail(nullptr, TDCFIE_E_ARG, "max_rhs out of range [1, 4096]");
-    if (o.precision != TDCFIE_BF16X3 && o.max_rhs > 8)
+    if (tensor && o.max_rhs != 64)
+        return fail(nullptr, TDCFIE_E_UNSUPPORTED, "the tensor-core paths march exactly 64 right-hand sides");
+    if (!tensor && o.max_rhs > 8)
         return fail(nullptr, TDCFIE_E_UNSUPPORTED, "FP64/FP32 paths march at most 8 right-hand sides together");
     if (o.solver != TDCFIE_SOLVE_DIRECT) return fail(nullptr, TDCFIE_E_UNSUPPORTED, "only the direct solver is built");
     tdcfie_t h = new tdcfie_s();
@@ -113,12 +117,18 @@ static tdcfie_status upload_mesh(tdcfie_t h) {
     return TDCFIE_OK;
 }
 
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 extern "C" tdcfie_status tdcfie_assemble(tdcfie_t h) {
     if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
+    double t0 = now_s();
     {
         tdcfie_status st0 = upload_mesh(h);
         if (st0 != TDCFIE_OK) return st0;
     }
+    h->asm_s[0] = now_s() - t0;
     const Mesh& M = h->mesh;
     cudaStream_t s = h->stream;
     const int64_t ne = M.ne, nc = M.nc, nv = M.nv, K = h->K;
@@ -139,18 +149,31 @@ extern "C" tdcfie_status tdcfie_assemble(tdcfie_t h) {
     CK(zalloc(&h->Psi, nv * nv));
     CK(zalloc(&h->Mst, ne * ne));
     CK(zalloc(&h->G, ne * ne));
+    CK(cudaStreamSynchronize(s));
+    t0 = now_s();
     launch_retarded_efie(h->dm, h->dt, h->K, h->T0, M.D, h->S, h->Phi, s);
     CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    h->asm_s[1] = now_s() - t0;
+    t0 = now_s();
     launch_retarded_mfie(h->dm, h->dt, h->K, M.D, h->MM, s);
     CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    h->asm_s[2] = now_s() - t0;
+    t0 = now_s();
     launch_static(h->dm, h->kappa, h->Zs, h->Psi, h->Mst, h->G, s);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
+    h->asm_s[3] = now_s() - t0;
+    t0 = now_s();
     tdcfie_status st = form_operators(h);
     if (st != TDCFIE_OK) return st;
+    h->asm_s[4] = now_s() - t0;
     h->assembled = true;
+    t0 = now_s();
     st = build_plan(h);
     if (st != TDCFIE_OK) return st;
+    h->asm_s[5] = now_s() - t0;
     return TDCFIE_OK;
 }
 
@@ -280,6 +303,12 @@ extern "C" tdcfie_status tdcfie_last_timing(tdcfie_t h, double* step_ms, double*
     if (history_ms) *history_ms = h->last_hist_ms;
     if (history_bytes) *history_bytes = h->hist_bytes;
     if (launches) *launches = h->last_launches;
+    return TDCFIE_OK;
+}
+
+extern "C" tdcfie_status tdcfie_assembly_timing(tdcfie_t h, double* seconds) {
+    if (!h || !seconds) return fail(h, TDCFIE_E_ARG, "NULL argument");
+    for (int i = 0; i < 6; ++i) seconds[i] = h->asm_s[i];
     return TDCFIE_OK;
 }
 

@@ -15,6 +15,13 @@
 //     breakpoint circles R = j dt cross the edge and into pieces of width <= 1, radial variable
 //     u = asinh(rho/|d|) (rho when the pair is coplanar) split at the breakpoint radii and into
 //     pieces of width <= 1; NANG and NRAD Gauss-Legendre points per piece;
+//   retarded pairs other than a triangle with itself, when the projection p is well outside the
+//     source triangle (every vertex at least two longest edges from p): polar coordinates about
+//     p over the triangle's own angular range only (two halves split at the middle vertex, angle
+//     variable psi = asinh(tan(theta - theta_f)) along the nearer boundary edge, split where
+//     breakpoint circles cross a boundary edge and into pieces of width <= 1), radius from the
+//     near to the far edge (split at breakpoint radii, u pieces of width <= 1); otherwise the
+//     signed sub-triangle form above;
 //   static pairs whose coarse parents share no vertex: 3 x 3 (fine-fine) and 3 x 7 (fine-coarse)
 //     product rules; same-parent pairs are coplanar (d = 0) and the curl kernel vanishes there.
 // Scatter: FP64 atomicAdd (order of summation is not fixed; results agree to rounding).
@@ -172,6 +179,137 @@ __device__ void polar(V3 x, V3 v0, V3 v1, V3 v2, const double* brk, int nb, bool
     }
 }
 
+
+__device__ __forceinline__ double cr2(double ax, double ay, double bx, double by) { return ax * by - ay * bx; }
+
+// Far form: integrate over the triangle's own angular range seen from p (no signed cancellation).
+template <class CB>
+__device__ void polar_far(V3 x, V3 v0, V3 v1, V3 v2, const double* brk, int nb, CB& cb) {
+    V3 n = cross(v1 - v0, v2 - v0);
+    n = (1.0 / nrm(n)) * n;
+    const double d = dot(x - v0, n), ad = fabs(d);
+    const V3 p = x - d * n;
+    const V3 vv[3] = {v0, v1, v2};
+    bool inside = true;
+    double lmax = 0.0, vmin = 1e300;
+    for (int i = 0; i < 3; ++i) {
+        if (dot(cross(vv[i] - p, vv[(i + 1) % 3] - p), n) < 0.0) inside = false;
+        lmax = fmax(lmax, nrm(vv[(i + 1) % 3] - vv[i]));
+        vmin = fmin(vmin, nrm(vv[i] - p));
+    }
+    if (inside || vmin < 2.0 * lmax) {
+        polar(x, v0, v1, v2, brk, nb, false, cb);
+        return;
+    }
+    V3 g = (1.0 / 3.0) * (v0 + v1 + v2) - p;
+    const V3 u = (1.0 / nrm(g)) * g, w = cross(n, u);
+    double X[3], Y[3], ph[3];
+    for (int i = 0; i < 3; ++i) {
+        X[i] = dot(vv[i] - p, u);
+        Y[i] = dot(vv[i] - p, w);
+        ph[i] = atan2(Y[i], X[i]);
+    }
+    int o[3] = {0, 1, 2};
+    for (int i = 1; i < 3; ++i) { int t = o[i], j = i - 1; while (j >= 0 && ph[o[j]] > ph[t]) { o[j + 1] = o[j]; --j; } o[j + 1] = t; }
+    const int L = o[0], Mv = o[1], H = o[2];
+    double rb[MAXB];
+    int nrb = 0;
+    for (int b = 0; b < nb; ++b)
+        if (brk[b] > ad) rb[nrb++] = sqrt(brk[b] * brk[b] - d * d);
+    for (int half = 0; half < 2; ++half) {
+        const double P0 = half == 0 ? ph[L] : ph[Mv], P1 = half == 0 ? ph[Mv] : ph[H];
+        if (!(P1 > P0)) continue;
+        const int ea[2] = {L, half == 0 ? L : Mv}, eb[2] = {H, half == 0 ? Mv : H};
+        double re_mid[2];
+        {
+            const double th = 0.5 * (P0 + P1), c = cos(th), sn = sin(th);
+            for (int ei = 0; ei < 2; ++ei) {
+                const double ax = X[ea[ei]], ay = Y[ea[ei]], bx = X[eb[ei]], by = Y[eb[ei]];
+                re_mid[ei] = cr2(ax, ay, bx - ax, by - ay) / cr2(c, sn, bx - ax, by - ay);
+            }
+        }
+        const int en = re_mid[0] < re_mid[1] ? 0 : 1;
+        const double nax = X[ea[en]], nay = Y[ea[en]], ndx = X[eb[en]] - nax, ndy = Y[eb[en]] - nay;
+        const double tf = -(nax * ndx + nay * ndy) / (ndx * ndx + ndy * ndy);
+        const double fx = nax + tf * ndx, fy = nay + tf * ndy;
+        const double hn = sqrt(fx * fx + fy * fy);
+        if (!(hn > 0.0)) continue;
+        const double thf = atan2(fy, fx);
+        double sp[4 * MAXB + 2];
+        int nsp = 0;
+        sp[nsp++] = P0;
+        for (int ei = 0; ei < 2; ++ei) {
+            const double ax = X[ea[ei]], ay = Y[ea[ei]], dx = X[eb[ei]] - ax, dy = Y[eb[ei]] - ay;
+            const double dd = dx * dx + dy * dy;
+            for (int q = 0; q < nrb; ++q) {
+                const double bq = ax * dx + ay * dy, cq = ax * ax + ay * ay - rb[q] * rb[q];
+                const double disc = bq * bq - dd * cq;
+                if (disc <= 0.0) continue;
+                const double sq = sqrt(disc);
+                const double ts[2] = {(-bq - sq) / dd, (-bq + sq) / dd};
+                for (int k = 0; k < 2; ++k) {
+                    if (ts[k] <= 0.0 || ts[k] >= 1.0) continue;
+                    const double ang = atan2(ay + ts[k] * dy, ax + ts[k] * dx);
+                    if (ang > P0 && ang < P1) sp[nsp++] = ang;
+                }
+            }
+        }
+        sp[nsp++] = P1;
+        sort_small(sp, nsp);
+        for (int pc = 0; pc + 1 < nsp; ++pc) {
+            const double S0 = asinh(tan(sp[pc] - thf)), S1 = asinh(tan(sp[pc + 1] - thf));
+            if (!(S1 > S0)) continue;
+            int nsub = (int)ceil((S1 - S0) / PIECE);
+            if (nsub < 1) nsub = 1;
+            const double hw = (S1 - S0) / nsub;
+            for (int sb = 0; sb < nsub; ++sb) {
+                for (int ga = 0; ga < NANG; ++ga) {
+                    const double psi = S0 + sb * hw + 0.5 * hw * (c_ax[ga] + 1.0);
+                    const double wth = 0.5 * hw * c_aw[ga] / cosh(psi);
+                    const double th = thf + atan(sinh(psi));
+                    const double c = cos(th), sn = sin(th);
+                    double re[2];
+                    for (int ei = 0; ei < 2; ++ei) {
+                        const double ax = X[ea[ei]], ay = Y[ea[ei]], bx = X[eb[ei]], by = Y[eb[ei]];
+                        re[ei] = cr2(ax, ay, bx - ax, by - ay) / cr2(c, sn, bx - ax, by - ay);
+                    }
+                    const double r0 = re[en], r1 = re[1 - en];
+                    const V3 om = c * u + sn * w;
+                    double rp[MAXB + 2];
+                    int nrp = 0;
+                    rp[nrp++] = r0;
+                    for (int q = 0; q < nrb; ++q)
+                        if (rb[q] > r0 && rb[q] < r1) rp[nrp++] = rb[q];
+                    rp[nrp++] = r1;
+                    sort_small(rp, nrp);
+                    for (int ri = 0; ri + 1 < nrp; ++ri) {
+                        const double a0 = rp[ri], a1 = rp[ri + 1];
+                        if (!(a1 > a0)) continue;
+                        if (ad > 0.0) {
+                            const double u0 = asinh(a0 / ad), u1 = asinh(a1 / ad);
+                            int ns = (int)ceil((u1 - u0) / PIECE);
+                            if (ns < 1) ns = 1;
+                            const double uw = (u1 - u0) / ns;
+                            for (int k = 0; k < ns; ++k)
+                                for (int gr = 0; gr < NRAD; ++gr) {
+                                    const double uu = u0 + k * uw + 0.5 * uw * (c_rx[gr] + 1.0);
+                                    const double rho = ad * sinh(uu), R = ad * cosh(uu);
+                                    cb(R, wth * 0.5 * uw * c_rw[gr] * rho * R, rho * om - d * n);
+                                }
+                        } else {
+                            const double rw = a1 - a0;
+                            for (int gr = 0; gr < NRAD; ++gr) {
+                                const double rho = a0 + 0.5 * rw * (c_rx[gr] + 1.0);
+                                cb(rho, wth * 0.5 * rw * c_rw[gr] * rho, rho * om);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ V3 tri_pt(const double (*r)[4], int q, V3 a, V3 b, V3 c) {
     return r[q][0] * a + r[q][1] * b + r[q][2] * c;
 }
@@ -251,7 +389,8 @@ __global__ void k_retarded_efie(DevMesh m, double dt, int K, double T0, double* 
         acc.dt = dt; acc.T0 = T0; acc.k0 = k0;
         acc.nk = min(LAGW, khi - k0 + 1);
         for (int i = 0; i < LAGW; ++i) { acc.s0[i] = 0; acc.s1[i][0] = acc.s1[i][1] = acc.s1[i][2] = 0; acc.p0[i] = 0; }
-        polar(x, v0, v1, v2, brk, nb, c == c2, acc);
+        if (c == c2) polar(x, v0, v1, v2, brk, nb, true, acc);
+        else polar_far(x, v0, v1, v2, brk, nb, acc);
         for (int i = 0; i < acc.nk; ++i) {
             const int k = k0 + i;
             atomicAdd(Phi + ((int64_t)k * m.nc + c) * m.nc + c2, wx * acc.p0[i] / (A * A2));
@@ -311,7 +450,7 @@ __global__ void k_retarded_mfie(DevMesh m, double dt, int K, double* __restrict_
         MfieAcc acc;
         acc.dt = dt; acc.k0 = k0; acc.nk = min(LAGW, khi - k0 + 1);
         for (int i = 0; i < LAGW; ++i) acc.m1[i][0] = acc.m1[i][1] = acc.m1[i][2] = 0.0;
-        polar(x, v0, v1, v2, brk, nb, false, acc);
+        polar_far(x, v0, v1, v2, brk, nb, acc);
         for (int i = 0; i < acc.nk; ++i) {
             const V3 m1 = {acc.m1[i][0], acc.m1[i][1], acc.m1[i][2]};
             if (m1.x == 0.0 && m1.y == 0.0 && m1.z == 0.0) continue;

@@ -67,6 +67,8 @@ void launch_static(const DevMesh& m, double kappa, double* Zs, double* Psi, doub
 // C = alpha op(A) op(B) + beta C, row-major, FP64 (cuBLAS DGEMM).
 void dgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, const double* A, int lda,
            const double* B, int ldb, double beta, double* C, int ldc);
+void sgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, float alpha, const float* A, int lda,
+           const float* B, int ldb, float beta, float* C, int ldc);
 // In-place inverse of an n x n row-major FP64 matrix (Gauss-Jordan, partial pivoting).
 // Returns 0 on success, 1 if a zero pivot was met.
 int invert(cudaStream_t s, double* A, int n, double* work);
@@ -79,6 +81,15 @@ void transpose(cudaStream_t s, const double* in, double* out, int rows, int cols
 
 // ---------------------------------------------------------------- hot path (march.cu)
 struct StepPlan;   // defined in march.cu
+
+struct Ctl {              // device-resident step state read by every kernel of a step
+    int64_t n;            // current step (1-based)
+    int64_t n0;           // step of the first output row of this tdcfie_step call
+    void* out;            // currents_out of this call (nullptr: discard)
+    int status;           // 0 ok, else a tdcfie_status recorded with bad_step
+    int64_t bad_step;
+    int timeout;          // set by a device-side bounded wait that ran out
+};
 }  // namespace tdc
 
 struct tdcfie_s {
@@ -108,6 +119,7 @@ struct tdcfie_s {
     int64_t R = 1;
     double* dexc = nullptr;   // R x 11: k(3), p(3), amp, t0, width, pad
     // timing
+    double asm_s[6] = {0, 0, 0, 0, 0, 0};   // upload, retarded EFIE, retarded MFIE, static, formation, plan
     double last_step_ms = 0, last_hist_ms = 0, hist_bytes = 0;
     int64_t last_launches = 0;
 };

@@ -28,6 +28,13 @@ void dgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, double alpha, 
                 A, lda, &beta, C, ldc);
 }
 
+// Row-major FP32 C (m x n) = alpha op(A) op(B) + beta C (cuBLAS SGEMM, pedantic FP32: no TF32).
+void sgemm(cudaStream_t s, bool ta, bool tb, int m, int n, int k, float alpha, const float* A, int lda,
+           const float* B, int ldb, float beta, float* C, int ldc) {
+    cublasSgemm(blas_for(s), tb ? CUBLAS_OP_T : CUBLAS_OP_N, ta ? CUBLAS_OP_T : CUBLAS_OP_N, n, m, k, &alpha, B, ldb,
+                A, lda, &beta, C, ldc);
+}
+
 // ---------------------------------------------------------------- Gauss-Jordan inverse
 // One block: find the pivot of column p among rows >= p, swap rows, scale the pivot row and save
 // the old column p (multipliers) in f.

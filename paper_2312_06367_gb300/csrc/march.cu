@@ -18,116 +18,41 @@
 #include <string>
 
 #include "internal.h"
+#include "plan.h"
 #include "umma.h"
 
 namespace tdc {
 
-struct Ctl {              // device-resident step state read by every kernel of a step
-    int64_t n;            // current step (1-based)
-    int64_t n0;           // step of the first output row of this tdcfie_step call
-    void* out;            // currents_out of this call (nullptr: discard)
-    int status;           // 0 ok, else TDCFIE_E_NONFINITE step recorded in bad_step
-    int64_t bad_step;
-};
-
-struct StepPlan {
-    int prec = TDCFIE_FP64;
-    int R = 1, ne = 0, nc = 0, K = 0, nblk = 0, ring = 0;
-    size_t esz = 8;
-    void* blocks = nullptr;      // nblk x ne x ne (path precision): -A, alpha L2, -T_1 .. -T_{K-1}
-    void* t0inv = nullptr;       // ne x ne
-    void* pinv = nullptr;        // nc x nc
-    void* E = nullptr;           // R x ne  (e_n)
-    void* Hv = nullptr;          // R x ne  (h_n)
-    void* ringbuf = nullptr;     // ring x R x ne
-    void* b = nullptr;           // R x ne
-    void* partial = nullptr;     // nblk x R x ne
-    void* w = nullptr;           // R x ne
-    void* z = nullptr;           // R x nc
-    void* u = nullptr;           // R x nc
-    const void** xptr = nullptr; // device array (unused for SIMT: computed in kernel)
-    Ctl* ctl = nullptr;
-    // rhs tables
-    int* fn_ptr = nullptr; int* fn_tri = nullptr; double* fn_phi = nullptr;
-    // bf16x3 path
-    Bf16x3Gemm* gemm = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
-    cudaEvent_t evA = nullptr, evB = nullptr;            // captured around the history sum
-    cudaGraphNode_t nodeA = nullptr, nodeB = nullptr;    // their record nodes in the step graph
-    std::vector<cudaEvent_t> hA, hB;                     // per-step events of a tdcfie_step call
-    int launches_per_step = 0;
-};
-
 // ---------------------------------------------------------------- plane-wave tests
-__constant__ double c7[7][4];
-__constant__ double c3[3][4];
-
+// Per edge m a list of quadrature points with a weighted basis vector: 7 points on each
+// triangle of f_m (degree-5 rule, coefficient w A f_m(x)) for e_m and 3 points on each fine
+// triangle of g_m (degree-2 rule, coefficient w A g_m(x)) for h_m.  Per step and wave r:
+//   e_m = sum_x c(x).p_r env_r(x, t_n),  h_m = sum_x c(x).(k_r x p_r) env_r(x, t_n),
+//   env_r(x, t) = amp_r exp(-((t - k_r.x - t0_r)/width_r)^2).
 template <typename T>
-__global__ void k_rhs(DevMesh m, const double* __restrict__ exc, int R, double dt, const Ctl* ctl,
-                      const int* __restrict__ fn_ptr, const int* __restrict__ fn_tri, const double* __restrict__ fn_phi,
-                      T* __restrict__ E, T* __restrict__ H) {
+__global__ void k_rhs(int ne, const double* __restrict__ exc, int R, double dt, const Ctl* ctl,
+                      const int* __restrict__ pptr, const T* __restrict__ px, const T* __restrict__ pc,
+                      const int* __restrict__ nE, T* __restrict__ E, T* __restrict__ H) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= m.ne * R) return;
-    const int r = idx / m.ne, mm = idx % m.ne;
-    const double t = (double)ctl->n * dt;
+    if (idx >= ne * R) return;
+    const int r = idx / ne, mm = idx % ne;
     const double* P = exc + 11 * r;   // k(3) p(3) amp t0 width
-    const double kx = P[0], ky = P[1], kz = P[2], px = P[3], py = P[4], pz = P[5];
-    const double amp = P[6], t0 = P[7], wid = P[8];
-    // h direction k x p
-    const double hx = ky * pz - kz * py, hy = kz * px - kx * pz, hz = kx * py - ky * px;
-    double e = 0.0;
-    // the two triangles of edge mm: walk both supports through fn_* is for BC; RWG support from E table
-    for (int side = 0; side < 2; ++side) {
-        const int c = side == 0 ? m.cplus_[mm] : m.cminus_[mm];
-        int j = 0;
-        for (; j < 3; ++j) if (m.tedge[3 * c + j] == mm) break;
-        const double* a = m.V + 3 * m.F[3 * c];
-        const double* b = m.V + 3 * m.F[3 * c + 1];
-        const double* cc = m.V + 3 * m.F[3 * c + 2];
-        const double ex = b[0] - a[0], ey = b[1] - a[1], ez = b[2] - a[2];
-        const double fx = cc[0] - a[0], fy = cc[1] - a[1], fz = cc[2] - a[2];
-        const double nx = ey * fz - ez * fy, ny = ez * fx - ex * fz, nz = ex * fy - ey * fx;
-        const double A = 0.5 * sqrt(nx * nx + ny * ny + nz * nz);
-        const double* o = m.V + 3 * m.F[3 * c + j];
-        const double s = m.tsign[3 * c + j] / (2.0 * A);
-        for (int q = 0; q < 7; ++q) {
-            const double x = c7[q][0] * a[0] + c7[q][1] * b[0] + c7[q][2] * cc[0];
-            const double y = c7[q][0] * a[1] + c7[q][1] * b[1] + c7[q][2] * cc[1];
-            const double zz = c7[q][0] * a[2] + c7[q][1] * b[2] + c7[q][2] * cc[2];
-            const double arg = (t - (kx * x + ky * y + kz * zz) - t0) / wid;
-            const double env = amp * exp(-arg * arg);
-            e += c7[q][3] * A * env * s * ((x - o[0]) * px + (y - o[1]) * py + (zz - o[2]) * pz);
-        }
+    const T kx = (T)P[0], ky = (T)P[1], kz = (T)P[2], qx = (T)P[3], qy = (T)P[4], qz = (T)P[5];
+    const T amp = (T)P[6], inv_w = (T)(1.0 / P[8]);
+    const T tt = (T)((double)ctl->n * dt - P[7]);
+    const T hx = ky * qz - kz * qy, hy = kz * qx - kx * qz, hz = kx * qy - ky * qx;   // k x p
+    T e = 0, h = 0;
+    const int b = pptr[mm], me = b + nE[mm], end = pptr[mm + 1];
+    for (int q = b; q < end; ++q) {
+        const T x = px[3 * q], y = px[3 * q + 1], z = px[3 * q + 2];
+        const T arg = (tt - (kx * x + ky * y + kz * z)) * inv_w;
+        const T env = amp * exp(-arg * arg);
+        const T cx = pc[3 * q], cy = pc[3 * q + 1], cz = pc[3 * q + 2];
+        if (q < me) e += env * (cx * qx + cy * qy + cz * qz);
+        else h += env * (cx * hx + cy * hy + cz * hz);
     }
-    double h = 0.0;
-    for (int q2 = fn_ptr[mm]; q2 < fn_ptr[mm + 1]; ++q2) {
-        const int ft = fn_tri[q2];
-        const double* ph = fn_phi + 3 * q2;
-        const double* w0 = m.fV + 3 * m.fF[3 * ft];
-        const double* w1 = m.fV + 3 * m.fF[3 * ft + 1];
-        const double* w2 = m.fV + 3 * m.fF[3 * ft + 2];
-        const double ex = w1[0] - w0[0], ey = w1[1] - w0[1], ez = w1[2] - w0[2];
-        const double fx = w2[0] - w0[0], fy = w2[1] - w0[1], fz = w2[2] - w0[2];
-        const double nx = ey * fz - ez * fy, ny = ez * fx - ex * fz, nz = ex * fy - ey * fx;
-        const double A = 0.5 * sqrt(nx * nx + ny * ny + nz * nz);
-        const double* W[3] = {w0, w1, w2};
-        for (int q = 0; q < 3; ++q) {
-            const double x = c3[q][0] * w0[0] + c3[q][1] * w1[0] + c3[q][2] * w2[0];
-            const double y = c3[q][0] * w0[1] + c3[q][1] * w1[1] + c3[q][2] * w2[1];
-            const double zz = c3[q][0] * w0[2] + c3[q][1] * w1[2] + c3[q][2] * w2[2];
-            double gx = 0, gy = 0, gz = 0;
-            for (int j = 0; j < 3; ++j) {
-                gx += ph[j] * (x - W[j][0]); gy += ph[j] * (y - W[j][1]); gz += ph[j] * (zz - W[j][2]);
-            }
-            const double arg = (t - (kx * x + ky * y + kz * zz) - t0) / wid;
-            const double env = amp * exp(-arg * arg);
-            h += c3[q][3] * A * env * (gx * hx + gy * hy + gz * hz) / (2.0 * A);
-        }
-    }
-    E[(int64_t)r * m.ne + mm] = (T)e;
-    H[(int64_t)r * m.ne + mm] = (T)h;
+    E[(int64_t)r * ne + mm] = e;
+    H[(int64_t)r * ne + mm] = h;
 }
 
 // ---------------------------------------------------------------- multi-block GEMV (SIMT)
@@ -251,17 +176,17 @@ static void launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
     const tdc::DevMesh& m = h->dm;
     const int R = p.R, ne = p.ne;
     const int tb = 256;
-    k_rhs<T><<<(ne * R + tb - 1) / tb, tb, 0, s>>>(m, h->dexc, R, h->dt, p.ctl, p.fn_ptr, p.fn_tri, p.fn_phi,
-                                                    (T*)p.E, (T*)p.Hv);
+    k_rhs<T><<<(ne * R + tb - 1) / tb, tb, 0, s>>>(ne, h->dexc, R, h->dt, p.ctl, p.pptr, (const T*)p.px,
+                                                    (const T*)p.pc, p.pnE, (T*)p.E, (T*)p.Hv);
     const int wpb = 8;   // warps per block
     dim3 g((ne + wpb - 1) / wpb, p.nblk);
 #define HIST(RM) k_history<T, RM><<<g, 32 * wpb, 0, s>>>((const T*)p.blocks, p.nblk, ne, R, p.ring, p.ctl, \
                                                            (const T*)p.E, (const T*)p.Hv, (const T*)p.ringbuf, (T*)p.partial)
 #define APPLY(RM, M, nr, nc_, x, y, rg) k_apply<T, RM><<<((nr) + wpb - 1) / wpb, 32 * wpb, 0, s>>>((const T*)(M), nr, nc_, R, (const T*)(x), (T*)(y), rg, p.ctl)
-    cudaEventRecord(p.evA, s);
+    cudaEventRecordWithFlags(p.evA, s, cudaEventRecordExternal);
     if (R == 1) HIST(1); else if (R <= 4) HIST(4); else HIST(8);
     k_reduce<T><<<(ne * R + tb - 1) / tb, tb, 0, s>>>((const T*)p.partial, p.nblk, ne, R, (T*)p.b);
-    cudaEventRecord(p.evB, s);
+    cudaEventRecordWithFlags(p.evB, s, cudaEventRecordExternal);
     if (R == 1) APPLY(1, p.t0inv, ne, ne, p.b, p.ringbuf, p.ring);
     else if (R <= 4) APPLY(4, p.t0inv, ne, ne, p.b, p.ringbuf, p.ring);
     else APPLY(8, p.t0inv, ne, ne, p.b, p.ringbuf, p.ring);
@@ -276,11 +201,27 @@ static void launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
     p.launches_per_step = 8;
 }
 
+// host wrappers used by the tensor-core step (umma.cu)
+void launch_rhs_f32(tdcfie_t h, StepPlan* p, float* E, float* H, cudaStream_t s) {
+    const int ne = p->ne, R = p->R, tb = 256;
+    k_rhs<float><<<(ne * R + tb - 1) / tb, tb, 0, s>>>(ne, h->dexc, R, h->dt, p->ctl, p->pptr, (const float*)p->px,
+                                                        (const float*)p->pc, p->pnE, E, H);
+}
+void launch_project_out_f32(tdcfie_t h, StepPlan* p, const float* yring, int ring, const float* u, cudaStream_t s) {
+    const int tb = 256;
+    k_project_out<float><<<(p->ne * p->R + tb - 1) / tb, tb, 0, s>>>(h->dm, p->R, ring, p->ctl, yring, u);
+}
+void launch_project_in_f32(tdcfie_t h, StepPlan* p, const float* yring, int ring, float* z, cudaStream_t s) {
+    const int tb = 256;
+    k_project_in<float><<<(p->nc * p->R + tb - 1) / tb, tb, 0, s>>>(h->dm, p->R, ring, p->ctl, yring, h->dtt, z);
+}
+void launch_advance(StepPlan* p, cudaStream_t s) { k_advance<<<1, 1, 0, s>>>(p->ctl); }
+
 void free_plan(tdcfie_t h) {
     StepPlan* p = h->plan;
     if (!p) return;
     void* bufs[] = {p->blocks, p->t0inv, p->pinv, p->E, p->Hv, p->ringbuf, p->b, p->partial, p->w, p->z, p->u,
-                    p->ctl, p->fn_ptr, p->fn_tri, p->fn_phi};
+                    p->ctl, p->pptr, p->pnE, p->px, p->pc};
     for (void* b : bufs) if (b) cudaFree(b);
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
@@ -316,42 +257,85 @@ tdcfie_status build_plan(tdcfie_t h) {
     p->ring = h->K - 1;
     p->esz = esize(p->prec);
     const int64_t ne = M.ne, nc = M.nc, R = p->R;
-    if (p->prec == TDCFIE_BF16X3) {
-        // the tensor-core path keeps FP32 vectors and splits matrices into bf16 hi/lo
-        p->esz = 4;
-    }
+    const bool tensor = p->prec == TDCFIE_BF16X3 || p->prec == TDCFIE_FP16X3;
+    if (tensor) p->esz = 4;   // the tensor-core paths keep FP32 vectors, 16-bit hi/lo matrices
     const size_t es = p->esz;
-    // rhs constant tables
+    // rhs quadrature tables (host, FP64), uploaded in the path precision
     {
         const double s15 = std::sqrt(15.0);
         const double a1 = (9.0 - 2.0 * s15) / 21.0, b1 = (6.0 + s15) / 21.0, w1 = (155.0 + s15) / 1200.0;
         const double a2 = (9.0 + 2.0 * s15) / 21.0, b2 = (6.0 - s15) / 21.0, w2 = (155.0 - s15) / 1200.0;
-        double r7[7][4] = {{1.0 / 3, 1.0 / 3, 1.0 / 3, 9.0 / 40.0}, {a1, b1, b1, w1}, {b1, a1, b1, w1}, {b1, b1, a1, w1},
-                           {a2, b2, b2, w2}, {b2, a2, b2, w2}, {b2, b2, a2, w2}};
-        double r3[3][4] = {{2.0 / 3, 1.0 / 6, 1.0 / 6, 1.0 / 3}, {1.0 / 6, 2.0 / 3, 1.0 / 6, 1.0 / 3},
-                           {1.0 / 6, 1.0 / 6, 2.0 / 3, 1.0 / 3}};
-        CK(cudaMemcpyToSymbolAsync(c7, r7, sizeof(r7), 0, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyToSymbolAsync(c3, r3, sizeof(r3), 0, cudaMemcpyHostToDevice, s));
-        // BC functions by function: (fine triangle, 3 fluxes)
-        std::vector<int> cnt(ne + 1, 0);
-        for (size_t e = 0; e < M.bc_fn.size(); ++e) cnt[M.bc_fn[e] + 1]++;
-        for (int64_t i = 0; i < ne; ++i) cnt[i + 1] += cnt[i];
-        std::vector<int> tri(M.bc_fn.size());
-        std::vector<double> ph(3 * M.bc_fn.size());
-        std::vector<int> fill(cnt.begin(), cnt.end() - 1);
-        for (int t = 0; t < M.nf; ++t)
-            for (int e = M.bc_ptr[t]; e < M.bc_ptr[t + 1]; ++e) {
-                const int pos = fill[M.bc_fn[e]]++;
-                tri[pos] = t;
-                for (int k = 0; k < 3; ++k) ph[3 * pos + k] = M.bc_phi[3 * e + k];
+        const double r7[7][4] = {{1.0 / 3, 1.0 / 3, 1.0 / 3, 9.0 / 40.0}, {a1, b1, b1, w1}, {b1, a1, b1, w1},
+                                 {b1, b1, a1, w1}, {a2, b2, b2, w2}, {b2, a2, b2, w2}, {b2, b2, a2, w2}};
+        const double r3[3][4] = {{2.0 / 3, 1.0 / 6, 1.0 / 6, 1.0 / 3}, {1.0 / 6, 2.0 / 3, 1.0 / 6, 1.0 / 3},
+                                 {1.0 / 6, 1.0 / 6, 2.0 / 3, 1.0 / 3}};
+        std::vector<std::vector<double>> pts(ne), cfs(ne);
+        std::vector<int> nE(ne, 0);
+        auto area = [](const double* a, const double* b, const double* c) {
+            const double ex = b[0] - a[0], ey = b[1] - a[1], ez = b[2] - a[2];
+            const double fx = c[0] - a[0], fy = c[1] - a[1], fz = c[2] - a[2];
+            const double nx = ey * fz - ez * fy, ny = ez * fx - ex * fz, nz = ex * fy - ey * fx;
+            return 0.5 * std::sqrt(nx * nx + ny * ny + nz * nz);
+        };
+        for (int c = 0; c < M.nc; ++c) {
+            const double* v[3] = {&M.V[3 * M.F[3 * c]], &M.V[3 * M.F[3 * c + 1]], &M.V[3 * M.F[3 * c + 2]]};
+            const double A = area(v[0], v[1], v[2]);
+            for (int j = 0; j < 3; ++j) {
+                const int m = M.tedge[3 * c + j];
+                const double sgn = M.tsign[3 * c + j] / (2.0 * A);
+                for (int q = 0; q < 7; ++q) {
+                    double x[3];
+                    for (int k = 0; k < 3; ++k) x[k] = r7[q][0] * v[0][k] + r7[q][1] * v[1][k] + r7[q][2] * v[2][k];
+                    for (int k = 0; k < 3; ++k) {
+                        pts[m].push_back(x[k]);
+                        cfs[m].push_back(r7[q][3] * A * sgn * (x[k] - v[j][k]));
+                    }
+                    nE[m]++;
+                }
             }
-        CK(cudaMalloc(&p->fn_ptr, sizeof(int) * (ne + 1)));
-        CK(cudaMalloc(&p->fn_tri, sizeof(int) * tri.size()));
-        CK(cudaMalloc(&p->fn_phi, sizeof(double) * ph.size()));
-        CK(cudaMemcpyAsync(p->fn_ptr, cnt.data(), sizeof(int) * (ne + 1), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(p->fn_tri, tri.data(), sizeof(int) * tri.size(), cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(p->fn_phi, ph.data(), sizeof(double) * ph.size(), cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));
+        }
+        for (int t = 0; t < M.nf; ++t) {
+            const double* v[3] = {&M.fV[3 * M.fF[3 * t]], &M.fV[3 * M.fF[3 * t + 1]], &M.fV[3 * M.fF[3 * t + 2]]};
+            const double A = area(v[0], v[1], v[2]);
+            for (int e = M.bc_ptr[t]; e < M.bc_ptr[t + 1]; ++e) {
+                const int m = M.bc_fn[e];
+                const double* ph = &M.bc_phi[3 * e];
+                for (int q = 0; q < 3; ++q) {
+                    double x[3];
+                    for (int k = 0; k < 3; ++k) x[k] = r3[q][0] * v[0][k] + r3[q][1] * v[1][k] + r3[q][2] * v[2][k];
+                    for (int k = 0; k < 3; ++k) {
+                        pts[m].push_back(x[k]);
+                        double g = 0.0;
+                        for (int j = 0; j < 3; ++j) g += ph[j] * (x[k] - v[j][k]);
+                        cfs[m].push_back(r3[q][3] * A * g / (2.0 * A));
+                    }
+                }
+            }
+        }
+        // e-points were pushed before any h-point of the same edge only if all coarse passes ran
+        // first, which they did (coarse loop precedes fine loop)
+        std::vector<int> ptr(ne + 1, 0);
+        for (int64_t m = 0; m < ne; ++m) ptr[m + 1] = ptr[m] + (int)(pts[m].size() / 3);
+        std::vector<double> X(3 * (size_t)ptr[ne]), C(3 * (size_t)ptr[ne]);
+        for (int64_t m = 0; m < ne; ++m) {
+            std::copy(pts[m].begin(), pts[m].end(), X.begin() + 3 * ptr[m]);
+            std::copy(cfs[m].begin(), cfs[m].end(), C.begin() + 3 * ptr[m]);
+        }
+        const size_t pes = (p->prec == TDCFIE_FP64) ? 8 : 4;
+        CK(cudaMalloc(&p->pptr, sizeof(int) * (ne + 1)));
+        CK(cudaMalloc(&p->pnE, sizeof(int) * ne));
+        CK(cudaMalloc(&p->px, pes * X.size()));
+        CK(cudaMalloc(&p->pc, pes * C.size()));
+        CK(cudaMemcpy(p->pptr, ptr.data(), sizeof(int) * (ne + 1), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(p->pnE, nE.data(), sizeof(int) * ne, cudaMemcpyHostToDevice));
+        if (pes == 8) {
+            CK(cudaMemcpy(p->px, X.data(), 8 * X.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(p->pc, C.data(), 8 * C.size(), cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> Xf(X.begin(), X.end()), Cf(C.begin(), C.end());
+            CK(cudaMemcpy(p->px, Xf.data(), 4 * Xf.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(p->pc, Cf.data(), 4 * Cf.size(), cudaMemcpyHostToDevice));
+        }
     }
     CK(cudaMalloc(&p->ctl, sizeof(Ctl)));
     CK(cudaMalloc(&p->E, es * R * ne));
@@ -361,7 +345,7 @@ tdcfie_status build_plan(tdcfie_t h) {
     CK(cudaMalloc(&p->partial, es * p->nblk * R * ne));
     CK(cudaMalloc(&p->z, es * R * nc));
     CK(cudaMalloc(&p->u, es * R * nc));
-    if (p->prec == TDCFIE_BF16X3) {
+    if (tensor) {
         tdcfie_status st = build_bf16x3(h, p);
         if (st != TDCFIE_OK) return st;
     } else {
@@ -399,9 +383,10 @@ tdcfie_status build_plan(tdcfie_t h) {
 tdcfie_status plan_reset(tdcfie_t h) {
     StepPlan* p = h->plan;
     cudaStream_t s = h->stream;
-    Ctl c{1, 1, nullptr, 0, 0};
+    Ctl c{1, 1, nullptr, 0, 0, 0};
     CK(cudaMemcpyAsync(p->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(p->ringbuf, 0, p->esz * p->ring * p->R * p->ne, s));
+    if (p->gemm) CK(reset_bf16x3(p->gemm, p->ring, s));
     CK(cudaStreamSynchronize(s));
     return TDCFIE_OK;
 }
@@ -474,6 +459,8 @@ tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out) {
     }
     h->last_hist_ms = cnt ? hs / cnt : 0.0;
     h->last_launches = nsteps * p->launches_per_step;
+    if (c.timeout)
+        return fail(h, TDCFIE_E_TIMEOUT, "a bounded device-side wait ran out (tensor-core pipeline)");
     if (c.status != 0)
         return fail(h, TDCFIE_E_NONFINITE, "non-finite current at step " + std::to_string(c.bad_step));
     return TDCFIE_OK;

@@ -1,0 +1,45 @@
+// Per-handle step plan shared by the SIMT (march.cu) and tensor-core (umma.cu) paths.
+#pragma once
+#include <vector>
+
+#include "internal.h"
+
+namespace tdc {
+struct Bf16x3Gemm;
+
+struct StepPlan {
+    int prec = TDCFIE_FP64;
+    int R = 1, ne = 0, nc = 0, K = 0, nblk = 0, ring = 0;
+    size_t esz = 8;
+    void* blocks = nullptr;      // nblk x ne x ne (path precision): -A, alpha L2, -T_1 .. -T_{K-1}
+    void* t0inv = nullptr;       // ne x ne
+    void* pinv = nullptr;        // nc x nc
+    void* E = nullptr;           // R x ne  (e_n)
+    void* Hv = nullptr;          // R x ne  (h_n)
+    void* ringbuf = nullptr;     // ring x R x ne
+    void* b = nullptr;           // R x ne
+    void* partial = nullptr;     // nblk x R x ne
+    void* w = nullptr;           // R x ne
+    void* z = nullptr;           // R x nc
+    void* u = nullptr;           // R x nc
+    const void** xptr = nullptr; // device array (unused for SIMT: computed in kernel)
+    Ctl* ctl = nullptr;
+    // rhs tables: per edge, quadrature points (x) and weighted basis vectors (c), e-points first
+    int* pptr = nullptr; int* pnE = nullptr; void* px = nullptr; void* pc = nullptr;
+    // bf16x3 path
+    Bf16x3Gemm* gemm = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    cudaEvent_t evA = nullptr, evB = nullptr;            // captured around the history sum
+    cudaGraphNode_t nodeA = nullptr, nodeB = nullptr;    // their record nodes in the step graph
+    std::vector<cudaEvent_t> hA, hB;                     // per-step events of a tdcfie_step call
+    int launches_per_step = 0;
+};
+
+
+void launch_rhs_f32(tdcfie_t h, StepPlan* p, float* E, float* H, cudaStream_t s);
+void launch_project_out_f32(tdcfie_t h, StepPlan* p, const float* yring, int ring, const float* u, cudaStream_t s);
+void launch_project_in_f32(tdcfie_t h, StepPlan* p, const float* yring, int ring, float* z, cudaStream_t s);
+void launch_advance(StepPlan* p, cudaStream_t s);
+}  // namespace tdc

@@ -9,7 +9,10 @@ coupling alpha and the plane-wave batch.  Names state what they are:
                      same pulse; FP32 history.
   sphere7680_r64     icosphere level 4 (5120 tri / 7680 edges), 64 Fibonacci directions with seeded
                      orthogonal polarisations (seed 2312063670), sigma 1, t0 8, dt 0.05, 2000 steps;
-                     BF16x3 tensor-core history.
+                     split-precision tensor-core history (fp16 hi/lo with power-of-two scaling, which
+                     meets 1e-5; bf16 hi/lo selectable).
+  sphere1920_r64     the same at icosphere level 3 (1280 tri / 1920 edges): a smaller case of the
+                     same tensor-core kernels whose blocks (634 MB) still exceed the L2 cache.
   ellipsoid12288     octasphere level 5 scaled to semi-axes (2, 1, 0.5) (8192 tri / 12288 edges),
                      dt 0.1, 1500 steps, GMRES tol 1e-8 (learned initial guess).
   batch32            32 seeded scatterers (spheres, ellipsoids, tori) of 480..12288 edges, dt 0.2,
@@ -34,11 +37,18 @@ def torus864_fp32():
                 pw=excitation.single(t0=8.0, sigma=2.0), precision="fp32")
 
 
-def sphere7680_r64(n_dir: int = 64):
+def sphere7680_r64(n_dir: int = 64, precision: str = "fp16x3"):
     V, F = meshes.icosphere(4)
     return dict(name="sphere7680_r64", V=V, F=F, dt=0.05, Nt=2000, alpha=1.0,
                 pw=excitation.fibonacci_batch(n_dir, seed=2312063670, t0=8.0, sigma=1.0),
-                precision="bf16x3")
+                precision=precision)
+
+
+def sphere1920_r64(n_dir: int = 64, precision: str = "fp16x3"):
+    V, F = meshes.icosphere(3)
+    return dict(name="sphere1920_r64", V=V, F=F, dt=0.05, Nt=2000, alpha=1.0,
+                pw=excitation.fibonacci_batch(n_dir, seed=2312063670, t0=8.0, sigma=1.0),
+                precision=precision)
 
 
 def ellipsoid12288():
