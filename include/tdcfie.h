@@ -142,6 +142,21 @@ tdcfie_status tdcfie_get_matrix(tdcfie_t h, int which, int64_t k, double* host_o
 tdcfie_status tdcfie_last_timing(tdcfie_t h, double* step_ms, double* history_ms, double* history_bytes,
                                  int64_t* kernel_launches);
 
+/*
+ * Stand-alone history sum of the MOT recurrence (Sec. IV-B, the sum over k of T_k y_{n-k}) for
+ * blocks the caller holds:
+ *     out[r][i] = sum_{q < nblk} sum_{j < n} blocks[q][i][j] x[q][r][j]
+ * blocks: DEVICE, nblk x n x n, row-major; x: DEVICE, nblk x R x n (block q's R vectors);
+ * out: DEVICE, R x n.  Element type double for TDCFIE_FP64 and float for TDCFIE_FP32 (FP32
+ * accumulation); 1 <= nblk <= 65535, 1 <= n <= 2^24, 1 <= R <= 8.  Per-block partial sums go to
+ * scratch taken with cudaMallocAsync / cudaFreeAsync on `stream` (cudaStream_t, NULL = legacy
+ * default stream); the blocks are then added in a fixed order, so results are deterministic.
+ * Asynchronous: returns after queueing.  Errors: TDCFIE_E_ARG, TDCFIE_E_UNSUPPORTED,
+ * TDCFIE_E_OOM, TDCFIE_E_CUDA (thread-local message in tdcfie_last_error(NULL)).
+ */
+tdcfie_status tdcfie_block_gemv(int precision, const void* blocks, int64_t nblk, int64_t n, const void* x, int64_t R,
+                                void* out, void* stream);
+
 /* Wall-clock seconds of the phases of the last tdcfie_assemble (host output, 6 values): mesh upload,
  * retarded EFIE quadrature, retarded MFIE quadrature, static quadrature, formation of the blocks
  * (projectors, preconditioner, T_k, inverses), path-precision copies. */

@@ -13,7 +13,24 @@ import numpy as np
 from . import _lib
 from ._lib import BF16X3, FP16X3, FP32, FP64, TdcfieError  # noqa: F401
 
-__all__ = ["Solver", "FP64", "FP32", "BF16X3", "FP16X3", "TdcfieError"]
+__all__ = ["Solver", "block_gemv", "FP64", "FP32", "BF16X3", "FP16X3", "TdcfieError"]
+
+
+def block_gemv(blocks, x, out=None, stream=None):
+    """out[r][i] = sum_q sum_j blocks[q][i][j] x[q][r][j] through tdcfie_block_gemv.
+
+    blocks (nblk, n, n) and x (nblk, R, n): contiguous CUDA tensors, both float64 or both float32."""
+    import torch
+    nblk, n, _ = blocks.shape
+    R = x.shape[1]
+    if out is None:
+        out = torch.empty((R, n), dtype=blocks.dtype, device=blocks.device)
+    prec = FP64 if blocks.dtype == torch.float64 else FP32
+    s = stream if stream is not None else torch.cuda.current_stream(blocks.device).cuda_stream
+    _lib.check(_lib.load().tdcfie_block_gemv(prec, ctypes.c_void_p(blocks.data_ptr()), nblk, n,
+                                             ctypes.c_void_p(x.data_ptr()), R, ctypes.c_void_p(out.data_ptr()),
+                                             ctypes.c_void_p(s)))
+    return out
 
 _PREC = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "fp16x3": FP16X3}
 

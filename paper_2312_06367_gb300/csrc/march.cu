@@ -35,7 +35,7 @@ __global__ void k_rhs(int ne, const double* __restrict__ exc, int R, double dt, 
                       const int* __restrict__ nE, T* __restrict__ E, T* __restrict__ H) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ne * R) return;
-    const int r = idx / ne, mm = idx % ne;
+    const int r = idx % R, mm = idx / R;     // waves fastest: a warp shares one edge's points
     const double* P = exc + 11 * r;   // k(3) p(3) amp t0 width
     const T kx = (T)P[0], ky = (T)P[1], kz = (T)P[2], qx = (T)P[3], qy = (T)P[4], qz = (T)P[5];
     const T amp = (T)P[6], inv_w = (T)(1.0 / P[8]);

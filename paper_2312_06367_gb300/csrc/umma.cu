@@ -343,16 +343,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 __global__ void k_fixup(const float* __restrict__ partial, const int* __restrict__ seg_ptr,
                         const int* __restrict__ seg_slot, int rows, int R, const Ctl* ctl, float* __restrict__ out,
                         int two_slots) {
-    const int t = blockIdx.x;
+    // grid (row tiles, R), BM threads: thread i sums the partials of row t*BM+i, right-hand side r
+    const int t = blockIdx.x, r = blockIdx.y, i = threadIdx.x;
+    const int row = t * BM + i;
+    if (row >= rows) return;
     float* o = out + (two_slots ? (ctl->n % 2) * (int64_t)R * rows : 0);
-    for (int e = threadIdx.x; e < BM * R; e += blockDim.x) {
-        const int r = e / BM, i = e % BM;
-        const int row = t * BM + i;
-        if (row >= rows) continue;
-        float s = 0.f;
-        for (int k = seg_ptr[t]; k < seg_ptr[t + 1]; ++k) s += partial[(int64_t)seg_slot[k] * R * BM + (int64_t)r * BM + i];
-        o[(int64_t)r * rows + row] = s;
-    }
+    float s = 0.f;
+    for (int k = seg_ptr[t]; k < seg_ptr[t + 1]; ++k) s += partial[(int64_t)seg_slot[k] * R * BM + (int64_t)r * BM + i];
+    o[(int64_t)r * rows + row] = s;
 }
 
 __device__ __forceinline__ uint16_t to16(float v, bool fp16) {
@@ -375,32 +373,38 @@ __device__ __forceinline__ float fill_scale(float m) {
 }
 
 // x: FP32 [R][n] (slot (n_step % 2) of a pair when pair != 0) -> 16-bit hi/lo [R][ld] into slot
-// `slot` (slot < 0: n_step % ring) with one scale per right-hand side; one block per r.
+// `slot` (slot < 0: n_step % ring) with one scale per right-hand side.  Grid (chunks, R): every
+// block reduces the whole vector r to its maximum (cheap, from L2) and writes its chunk.
+constexpr int SPLIT_CHUNK = 1024;
 __global__ void k_split_vec(const float* __restrict__ x, int n, int R, int ld, uint16_t* __restrict__ hi,
                             uint16_t* __restrict__ lo, float* __restrict__ inv_scale, int slot, int ring, int pair,
                             int fp16, const Ctl* ctl) {
     __shared__ float red[256];
-    const int r = blockIdx.x;
+    const int r = blockIdx.y;
     const int64_t step = ctl->n;
     const float* xr = x + (pair ? (step % 2) * (int64_t)R * n : 0) + (int64_t)r * n;
     const int sl = slot >= 0 ? slot : (int)(step % ring);
-    float m = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(xr[i]));
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+    float sc = 1.f;
+    if (fp16) {
+        float m = 0.f;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(xr[i]));
+        red[threadIdx.x] = m;
         __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+            __syncthreads();
+        }
+        sc = fill_scale(red[0]);
     }
-    const float sc = fp16 ? fill_scale(red[0]) : 1.f;
     const int64_t off = (int64_t)sl * R * ld + (int64_t)r * ld;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int i0 = blockIdx.x * SPLIT_CHUNK, i1 = min(n, i0 + SPLIT_CHUNK);
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const float v = xr[i] * sc;
         const uint16_t h = to16(v, fp16);
         hi[off + i] = h;
         lo[off + i] = to16(v - from16(h, fp16), fp16);
     }
-    if (threadIdx.x == 0 && inv_scale) inv_scale[(int64_t)sl * R + r] = 1.f / sc;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && inv_scale) inv_scale[(int64_t)sl * R + r] = 1.f / sc;
 }
 
 // FP64 matrix block (rows x cols, times `scale`) -> 16-bit hi/lo [rows][ld], zero padding;
@@ -639,7 +643,7 @@ tdcfie_status build_bf16x3(tdcfie_t h, StepPlan* p) {
     g->proj.a.sA = g->sAp; g->proj.a.sX = g->sXz;
     CKB(cudaFuncSetAttribute(k_umma_bf16x3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<64>::SMEM));
     CKB(cudaStreamSynchronize(s));
-    // algorithmic bytes of the history sum: every block (hi + lo) once, and its R vectors
+    // algorithmic bytes of the history GEMM: every block (hi + lo) once, and its R vectors
     h->hist_bytes = (double)nblk * ne * ne * 4.0 + (double)nblk * R * ne * 4.0;
     return TDCFIE_OK;
 }
@@ -653,24 +657,28 @@ void launch_step_bf16x3(tdcfie_t h, StepPlan* p, cudaStream_t s) {
     const int R = p->R, ne = p->ne, nc = p->nc, ring = p->ring, ld = g->ld, ldc = g->ldc;
     const int f16 = g->fp16 ? 1 : 0;
     // plane-wave tests -> e, h slots of the history operand
+    const dim3 gv((ne + SPLIT_CHUNK - 1) / SPLIT_CHUNK, R), gz((nc + SPLIT_CHUNK - 1) / SPLIT_CHUNK, R);
     launch_rhs_f32(h, p, g->E, g->H, s);
-    k_split_vec<<<R, 256, 0, s>>>(g->E, ne, R, ld, g->Xh, g->Xl, g->sXh, ring, ring, 0, f16, p->ctl);
-    k_split_vec<<<R, 256, 0, s>>>(g->H, ne, R, ld, g->Xh, g->Xl, g->sXh, ring + 1, ring, 0, f16, p->ctl);
-    // history sum b_n = -A e_n + alpha L2 h_n - sum_k T_k y_{n-k}
+    k_split_vec<<<gv, 256, 0, s>>>(g->E, ne, R, ld, g->Xh, g->Xl, g->sXh, ring, ring, 0, f16, p->ctl);
+    k_split_vec<<<gv, 256, 0, s>>>(g->H, ne, R, ld, g->Xh, g->Xl, g->sXh, ring + 1, ring, 0, f16, p->ctl);
+    // history sum b_n = -A e_n + alpha L2 h_n - sum_k T_k y_{n-k}  (events bracket the GEMM alone)
     cudaEventRecordWithFlags(p->evA, s, cudaEventRecordExternal);
     run_gemm(g->hist, s);
-    k_fixup<<<g->hist.a.rtiles, 256, 0, s>>>(g->partial, g->hist.seg_ptr, g->hist.seg_slot, ne, R, p->ctl, g->b32, 0);
     cudaEventRecordWithFlags(p->evB, s, cudaEventRecordExternal);
-    k_split_vec<<<R, 256, 0, s>>>(g->b32, ne, R, ld, g->bh, g->bl, g->sXb, 0, ring, 0, f16, p->ctl);
+    k_fixup<<<dim3(g->hist.a.rtiles, R), BM, 0, s>>>(g->partial, g->hist.seg_ptr, g->hist.seg_slot, ne, R, p->ctl,
+                                                     g->b32, 0);
+    k_split_vec<<<gv, 256, 0, s>>>(g->b32, ne, R, ld, g->bh, g->bl, g->sXb, 0, ring, 0, f16, p->ctl);
     // y_n = T_0^-1 b_n  (FP32 in y32[n % 2]; 16-bit hi/lo into history slot n % ring)
     run_gemm(g->solve, s);
-    k_fixup<<<g->solve.a.rtiles, 256, 0, s>>>(g->partial, g->solve.seg_ptr, g->solve.seg_slot, ne, R, p->ctl, g->y32, 1);
-    k_split_vec<<<R, 256, 0, s>>>(g->y32, ne, R, ld, g->Xh, g->Xl, g->sXh, -1, ring, 1, f16, p->ctl);
+    k_fixup<<<dim3(g->solve.a.rtiles, R), BM, 0, s>>>(g->partial, g->solve.seg_ptr, g->solve.seg_slot, ne, R,
+                                                      p->ctl, g->y32, 1);
+    k_split_vec<<<gv, 256, 0, s>>>(g->y32, ne, R, ld, g->Xh, g->Xl, g->sXh, -1, ring, 1, f16, p->ctl);
     // projector: z = Sigma^T w_n, u = (Sigma^T Sigma)^+ z, j_n = y_n + Sigma u
     launch_project_in_f32(h, p, g->y32, 2, g->z32, s);
-    k_split_vec<<<R, 256, 0, s>>>(g->z32, nc, R, ldc, g->zh, g->zl, g->sXz, 0, ring, 0, f16, p->ctl);
+    k_split_vec<<<gz, 256, 0, s>>>(g->z32, nc, R, ldc, g->zh, g->zl, g->sXz, 0, ring, 0, f16, p->ctl);
     run_gemm(g->proj, s);
-    k_fixup<<<g->proj.a.rtiles, 256, 0, s>>>(g->partial, g->proj.seg_ptr, g->proj.seg_slot, nc, R, p->ctl, g->u32, 0);
+    k_fixup<<<dim3(g->proj.a.rtiles, R), BM, 0, s>>>(g->partial, g->proj.seg_ptr, g->proj.seg_slot, nc, R, p->ctl,
+                                                     g->u32, 0);
     launch_project_out_f32(h, p, g->y32, 2, g->u32, s);
     launch_advance(p, s);
     p->launches_per_step = 16;

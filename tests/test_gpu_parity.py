@@ -131,3 +131,20 @@ def test_torus_fp32_small():
     _, _, j_ref = _oracle(V, F, 0.5, 60, pw)
     _, j = _gpu(V, F, 0.5, 60, pw, "fp32")
     assert rel(j, j_ref) < 1e-5
+
+
+@pytest.mark.parametrize("dtype,tol", [("float64", 1e-13), ("float32", 1e-5)])
+@pytest.mark.parametrize("nblk,n,R", [(1, 1, 1), (13, 480, 1), (5, 97, 3), (42, 300, 8)])
+def test_block_gemv_matches_numpy(dtype, tol, nblk, n, R):
+    """Stand-alone history-sum entry point against a plain numpy FP64 evaluation."""
+    import torch
+    from paper_2312_06367_gb300 import block_gemv
+    rng = np.random.default_rng(nblk * 1000 + n + R)
+    B = rng.standard_normal((nblk, n, n))
+    X = rng.standard_normal((nblk, R, n))
+    ref = np.einsum("qij,qrj->ri", B, X)
+    td = getattr(torch, dtype)
+    out = block_gemv(torch.tensor(B, dtype=td, device="cuda"), torch.tensor(X, dtype=td, device="cuda"))
+    torch.cuda.synchronize()
+    got = out.double().cpu().numpy()
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
