@@ -157,6 +157,24 @@ tdcfie_status tdcfie_last_timing(tdcfie_t h, double* step_ms, double* history_ms
 tdcfie_status tdcfie_block_gemv(int precision, const void* blocks, int64_t nblk, int64_t n, const void* x, int64_t R,
                                 void* out, void* stream);
 
+/*
+ * tdcfie_block_gemv for callers that cannot allocate device memory at the time of the call (for
+ * example a thread of a process in which another thread holds a global-mode stream capture, a
+ * service whose allocator has reserved nearly all device memory, or a loop that cannot take an
+ * allocation's implicit synchronisation).  The paper has no counterpart; this is a library
+ * service.  Same arguments, layouts, arithmetic and result as tdcfie_block_gemv, but the
+ * per-block partial sums go to a file-scope static device array of 32 MiB that every GPU loading
+ * the library holds until the process exits: nblk * R * n must not exceed 4194304 (FP64) or
+ * 8388608 (FP32), else TDCFIE_E_ARG with a message.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and every partial sum a call reads it has written
+ * first, so nothing needs clearing between calls; calls whose executions overlap on the GPU
+ * (different streams, or graphs replayed concurrently) race on it and must be serialised.
+ */
+tdcfie_status tdcfie_block_gemv_noalloc(int precision, const void* blocks, int64_t nblk, int64_t n, const void* x,
+                                        int64_t R, void* out, void* stream);
+
 /* Wall-clock seconds of the phases of the last tdcfie_assemble (host output, 6 values): mesh upload,
  * retarded EFIE quadrature, retarded MFIE quadrature, static quadrature, formation of the blocks
  * (projectors, preconditioner, T_k, inverses), path-precision copies. */

@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import BF16X3, FP16X3, FP32, FP64, TdcfieError  # noqa: F401
 
-__all__ = ["Solver", "block_gemv", "FP64", "FP32", "BF16X3", "FP16X3", "TdcfieError"]
+__all__ = ["Solver", "block_gemv", "block_gemv_noalloc", "FP64", "FP32", "BF16X3", "FP16X3", "TdcfieError"]
 
 
 def block_gemv(blocks, x, out=None, stream=None):
@@ -30,6 +30,20 @@ def block_gemv(blocks, x, out=None, stream=None):
     _lib.check(_lib.load().tdcfie_block_gemv(prec, ctypes.c_void_p(blocks.data_ptr()), nblk, n,
                                              ctypes.c_void_p(x.data_ptr()), R, ctypes.c_void_p(out.data_ptr()),
                                              ctypes.c_void_p(s)))
+    return out
+
+
+def block_gemv_noalloc(blocks, x, out, stream=None):
+    """block_gemv through tdcfie_block_gemv_noalloc: no device allocation by the library (the caller
+    provides `out`; partial sums use the library's 32 MiB static device scratch)."""
+    import torch
+    nblk, n, _ = blocks.shape
+    R = x.shape[1]
+    prec = FP64 if blocks.dtype == torch.float64 else FP32
+    s = stream if stream is not None else torch.cuda.current_stream(blocks.device).cuda_stream
+    _lib.check(_lib.load().tdcfie_block_gemv_noalloc(prec, ctypes.c_void_p(blocks.data_ptr()), nblk, n,
+                                                     ctypes.c_void_p(x.data_ptr()), R,
+                                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s)))
     return out
 
 _PREC = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "fp16x3": FP16X3}

@@ -54,6 +54,7 @@ SIGNATURES = [
     ("tdcfie_last_timing", _I, [_P, _P, _P, _P, _P]),
     ("tdcfie_assembly_timing", _I, [_P, _P]),
     ("tdcfie_block_gemv", _I, [_I, _P, _I64, _I64, _P, _I64, _P, _P]),
+    ("tdcfie_block_gemv_noalloc", _I, [_I, _P, _I64, _I64, _P, _I64, _P, _P]),
     ("tdcfie_destroy", _I, [_P]),
     ("tdcfie_last_error", ctypes.c_char_p, [_P]),
 ]

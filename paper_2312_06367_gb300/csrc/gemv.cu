@@ -4,6 +4,8 @@
 // blocks in a fixed order (deterministic result).
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace tdc {
@@ -88,5 +90,63 @@ extern "C" tdcfie_status tdcfie_block_gemv(int precision, const void* blocks, in
     cudaError_t e2 = cudaFreeAsync(partial, s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "block GEMV launch");
     if (e2 != cudaSuccess) return cuda_fail(nullptr, e2, "cudaFreeAsync (block GEMV scratch)");
+    return TDCFIE_OK;
+}
+
+// ---------------------------------------------------------------- variant without allocation
+// Some callers cannot allocate device memory when they need this sum: a thread of a process in
+// which another thread holds a global-mode stream capture (cudaMalloc is not permitted then),
+// services whose caching allocator has reserved nearly all of the HBM up front, or loops that
+// cannot take the implicit synchronisation of an allocation.  For them the per-block partial sums
+// live in this file-scope device array.  Every GPU that loads the library holds it (32 MiB) until
+// the process exits.  In host code the name below is only a host-side stand-in for the array;
+// the kernels receive the device address obtained with cudaGetSymbolAddress.
+namespace tdc {
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_block_gemv_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void* g_scratch_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_scratch_mu;
+
+// device address of the scratch array on the current device (looked up once per device)
+static cudaError_t scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_block_gemv_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+}  // namespace tdc
+
+extern "C" tdcfie_status tdcfie_block_gemv_noalloc(int precision, const void* blocks, int64_t nblk, int64_t n,
+                                                   const void* x, int64_t R, void* out, void* stream) {
+    tdcfie_status st = check_gemv(precision, blocks, nblk, n, x, R, out);
+    if (st != TDCFIE_OK) return st;
+    const size_t es = precision == TDCFIE_FP64 ? 8 : 4;
+    const double need = (double)es * (double)nblk * (double)R * (double)n;
+    if (need > (double)NOALLOC_SCRATCH_BYTES)
+        return fail(nullptr, TDCFIE_E_ARG,
+                    "tdcfie_block_gemv_noalloc: nblk * R * n * element size exceeds the 32 MiB static scratch "
+                    "(at most 4194304 FP64 or 8388608 FP32 partial sums); use tdcfie_block_gemv");
+    void* partial = nullptr;
+    cudaError_t e = scratch_address(&partial);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress (static block GEMV scratch)");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == TDCFIE_FP64)
+        e = launch_block_gemv<double>((const double*)blocks, nblk, n, (const double*)x, (int)R, (double*)out,
+                                      (double*)partial, s);
+    else
+        e = launch_block_gemv<float>((const float*)blocks, nblk, n, (const float*)x, (int)R, (float*)out,
+                                     (float*)partial, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "block GEMV launch");
     return TDCFIE_OK;
 }
