@@ -43,7 +43,10 @@ typedef enum {
  * 64 right-hand sides; FP64 and FP32 at most 8. */
 typedef enum { TDCFIE_FP64 = 0, TDCFIE_FP32 = 1, TDCFIE_BF16X3 = 2, TDCFIE_FP16X3 = 3 } tdcfie_precision;
 /* Solve with T_0 each step: DIRECT = explicit FP64-factored inverse applied in path precision;
- * GMRES = restarted GMRES on T_0 (path-precision matvec, FP64 residual and orthogonalisation). */
+ * GMRES = restarted GMRES on T_0: inner Arnoldi cycles of gmres_restart iterations with the
+ * path-precision T_0 and CGS2 orthogonalisation in FP64, outer cycles restart from the true FP64
+ * residual until ||b - T_0 y|| <= gmres_tol ||b|| (at most gmres_maxit inner iterations in all).
+ * Initial guess: ZERO, PREV (y_{n-1}) or MLP (learned, see tdcfie_mlp_*).  FP64 and FP32 paths. */
 typedef enum { TDCFIE_SOLVE_DIRECT = 0, TDCFIE_SOLVE_GMRES = 1 } tdcfie_solver;
 typedef enum { TDCFIE_GUESS_ZERO = 0, TDCFIE_GUESS_PREV = 1, TDCFIE_GUESS_MLP = 2 } tdcfie_guess;
 
@@ -112,6 +115,48 @@ tdcfie_status tdcfie_set_excitation(tdcfie_t h, const tdcfie_plane_waves* exc);
  * The march state (step counter, ring of the last K-1 y, the last y) persists across calls.
  */
 tdcfie_status tdcfie_step(tdcfie_t h, int64_t nsteps, void* currents_out);
+
+/* tdcfie_step that also writes the auxiliary unknown y_n (Eq. y_expansion coefficients) of every
+ * step to y_out (DEVICE, nsteps x R x N_E, path dtype; NULL = none).  FP64 and FP32 paths. */
+tdcfie_status tdcfie_step_y(tdcfie_t h, int64_t nsteps, void* currents_out, void* y_out);
+
+/* GMRES statistics since the last set_excitation (opts.solver = TDCFIE_SOLVE_GMRES): total inner
+ * iterations over all steps and right-hand sides, steps solved, the largest per-step count, and the
+ * number of (step, right-hand side) solves left above gmres_tol after the last outer cycle. */
+tdcfie_status tdcfie_gmres_stats(tdcfie_t h, int64_t* inner_iterations, int64_t* steps, int64_t* max_per_step,
+                                 int64_t* not_converged);
+
+/*
+ * Learned initial guess for the GMRES solve (an extension: the paper solves with T_0 directly).
+ * For unknown m of right-hand side r at step n the features are x = (y_{n-1}, ..., y_{n-8})_{r,m} / s,
+ * s = RMS over edges of y_{n-1} for that r (1 if zero), and the guess is s f(x) with the network
+ *   f(x) = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3,  W1 64 x 8, W2 64 x 64, w3 64.
+ * Parameters: 4801 float32 in the order W1 (row-major), b1, W2 (row-major), b2, w3, b3.
+ * Samples: X n x 8 float32 features (row-major), Y n float32 targets.
+ */
+#define TDCFIE_MLP_NPARAM 4801
+
+/* Gradient of the loss (1/2n) sum_s (f(X_s) - Y_s)^2 at params (all DEVICE pointers): grad receives
+ * 4801 floats, loss one float.  FP32 arithmetic.  Enqueued on stream (NULL = legacy stream). */
+tdcfie_status tdcfie_mlp_grad(const float* params, const float* X, const float* Y, int64_t n, float* grad,
+                              float* loss, void* stream);
+
+/* Adam (beta 0.9 / 0.999, eps 1e-8, rate lr) on the same loss over mini-batches of `batch` samples
+ * for `epochs` passes; each pass starts at a seeded rotation of the sample order.  params (DEVICE)
+ * is updated in place; loss_history (HOST, epochs floats, or NULL) receives each pass's mean
+ * mini-batch loss and makes the call synchronous.  Allocates its optimiser state from the stream's
+ * pool and frees it before returning. */
+tdcfie_status tdcfie_mlp_train(float* params, const float* X, const float* Y, int64_t n, int epochs, int64_t batch,
+                               float lr, uint64_t seed, float* loss_history, void* stream);
+
+/* out[s] = f(X_s) with the weights rounded to float16 (the form used inside the march), FP32
+ * arithmetic; DEVICE pointers. */
+tdcfie_status tdcfie_mlp_predict(const float* params, const float* X, int64_t n, float* out, void* stream);
+
+/* Load network parameters (HOST, 4801 floats) into a handle assembled with solver GMRES and
+ * guess TDCFIE_GUESS_MLP (which needs K - 1 >= 8).  Synchronous.  Until loaded the weights are zero
+ * and so is the guess. */
+tdcfie_status tdcfie_mlp_load(tdcfie_t h, const float* params);
 
 /* Whole march: set_excitation, then nt steps into currents_out.  out_on_host != 0: currents_out is a
  * HOST buffer (pinned or pageable) and the device-to-host copy is part of the call. */

@@ -1,0 +1,71 @@
+"""Plain FP64 reference of the learned initial guess (TEST INFRASTRUCTURE ONLY; see oracle/__init__.py).
+
+The paper has no learned component; this follows the per-unknown guess of the build's workload:
+features of unknown m at step n are its last eight values (y_{n-1..n-8})_m divided by
+s_n = RMS_m (y_{n-1})_m; the network predicts y_{n,m} / s_n.  Network 8 -> 64 -> 64 -> 1, tanh
+on both hidden layers, squared-error loss (1/2N) sum (out - target)^2.
+Parameter vector layout (4801 floats): W1 (64 x 8), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+NIN, NH = 8, 64
+SIZES = [("W1", (NH, NIN)), ("b1", (NH,)), ("W2", (NH, NH)), ("b2", (NH,)), ("W3", (NH,)), ("b3", (1,))]
+NPARAM = sum(int(np.prod(s)) for _, s in SIZES)
+
+
+def unpack(theta):
+    out, o = {}, 0
+    for name, shape in SIZES:
+        n = int(np.prod(shape))
+        out[name] = np.asarray(theta[o:o + n], dtype=np.float64).reshape(shape)
+        o += n
+    return out
+
+
+def forward(theta, X):
+    p = unpack(theta)
+    h1 = np.tanh(X @ p["W1"].T + p["b1"])
+    h2 = np.tanh(h1 @ p["W2"].T + p["b2"])
+    return h2 @ p["W3"] + p["b3"][0], (h1, h2)
+
+
+def loss_and_grad(theta, X, Y):
+    """Loss (1/2N) sum (f(x) - y)^2 and its gradient with respect to the parameter vector."""
+    p = unpack(theta)
+    N = X.shape[0]
+    out, (h1, h2) = forward(theta, X)
+    d = (out - Y) / N
+    loss = 0.5 * np.sum((out - Y) ** 2) / N
+    g = {"W3": h2.T @ d, "b3": np.array([d.sum()])}
+    dz2 = np.outer(d, p["W3"]) * (1.0 - h2 ** 2)
+    g["W2"] = dz2.T @ h1
+    g["b2"] = dz2.sum(axis=0)
+    dz1 = (dz2 @ p["W2"]) * (1.0 - h1 ** 2)
+    g["W1"] = dz1.T @ X
+    g["b1"] = dz1.sum(axis=0)
+    return loss, np.concatenate([g[name].reshape(-1) for name, _ in SIZES])
+
+
+def features(y_hist):
+    """y_hist: (9, ne, R) = y_{n-8} .. y_n.  Returns X (ne R, 8) = y_{n-1..n-8}/s_n and target y_n/s_n."""
+    prev = y_hist[-2]                                   # y_{n-1}
+    s = np.sqrt(np.mean(prev ** 2, axis=0))             # per right-hand side
+    s = np.where(s > 0, s, 1.0)
+    X = np.stack([y_hist[-2 - k] / s for k in range(8)], axis=-1)   # (ne, R, 8)
+    Y = y_hist[-1] / s
+    return X.reshape(-1, 8), Y.reshape(-1), s
+
+
+def init_params(seed: int):
+    """Seeded initial parameters: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for name, shape in SIZES:
+        if name.startswith("W"):
+            fan_in = shape[-1] if len(shape) == 2 else NH
+            parts.append(rng.uniform(-1.0, 1.0, size=shape).reshape(-1) / np.sqrt(fan_in))
+        else:
+            parts.append(np.zeros(int(np.prod(shape))))
+    return np.concatenate(parts)

@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import BF16X3, FP16X3, FP32, FP64, TdcfieError  # noqa: F401
 
-__all__ = ["Solver", "block_gemv", "block_gemv_noalloc", "FP64", "FP32", "BF16X3", "FP16X3", "TdcfieError"]
+__all__ = ["Solver", "block_gemv", "block_gemv_noalloc", "mlp_grad", "mlp_train", "mlp_predict", "FP64", "FP32", "BF16X3", "FP16X3", "TdcfieError"]
 
 
 def block_gemv(blocks, x, out=None, stream=None):
@@ -46,6 +46,48 @@ def block_gemv_noalloc(blocks, x, out, stream=None):
                                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s)))
     return out
 
+
+def _stream(t, stream):
+    import torch
+    return stream if stream is not None else torch.cuda.current_stream(t.device).cuda_stream
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mlp_grad(params, X, Y, stream=None):
+    """(grad, loss) of the learned-guess network's loss (1/2n) sum (f(X) - Y)^2 through tdcfie_mlp_grad.
+
+    params (4801,), X (n, 8), Y (n,): contiguous float32 CUDA tensors."""
+    import torch
+    grad = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _lib.check(_lib.load().tdcfie_mlp_grad(_vp(params), _vp(X), _vp(Y), X.shape[0], _vp(grad), _vp(loss),
+                                           ctypes.c_void_p(_stream(params, stream))))
+    return grad, loss
+
+
+def mlp_train(params, X, Y, epochs: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0, stream=None):
+    """Adam training in place through tdcfie_mlp_train; returns the per-pass mean loss (numpy)."""
+    hist = np.zeros(int(epochs), dtype=np.float32)
+    _lib.check(_lib.load().tdcfie_mlp_train(_vp(params), _vp(X), _vp(Y), X.shape[0], int(epochs), int(batch),
+                                            float(lr), int(seed), _lib._ptr(hist),
+                                            ctypes.c_void_p(_stream(params, stream))))
+    return hist
+
+
+def mlp_predict(params, X, stream=None):
+    """f(X) with FP16-rounded weights through tdcfie_mlp_predict."""
+    import torch
+    out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _lib.check(_lib.load().tdcfie_mlp_predict(_vp(params), _vp(X), X.shape[0], _vp(out),
+                                              ctypes.c_void_p(_stream(params, stream))))
+    return out
+
+
+_SOLVE = {"direct": _lib.SOLVE_DIRECT, "gmres": _lib.SOLVE_GMRES}
+_GUESS = {"zero": _lib.GUESS_ZERO, "prev": _lib.GUESS_PREV, "mlp": _lib.GUESS_MLP}
 _PREC = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "fp16x3": FP16X3}
 
 
@@ -53,7 +95,8 @@ class Solver:
     """One scatterer: create (host tables) -> assemble (device, FP64) -> march/step (hot path)."""
 
     def __init__(self, V, F, dt: float, nt: int, alpha: float = 1.0, precision="fp64", R: int = 1,
-                 stream=None, device: int = 0):
+                 stream=None, device: int = 0, solver: str = "direct", gmres_tol: float | None = None,
+                 gmres_restart: int | None = None, gmres_maxit: int | None = None, guess: str | None = None):
         L = _lib.load()
         self._V = np.ascontiguousarray(V, dtype=np.float64)
         self._F = np.ascontiguousarray(F, dtype=np.int32)
@@ -62,6 +105,15 @@ class Solver:
         o.max_rhs = int(R)
         o.device = int(device)
         o.stream = ctypes.c_void_p(stream) if stream else None
+        o.solver = _SOLVE[solver]
+        if gmres_tol is not None:
+            o.gmres_tol = float(gmres_tol)
+        if gmres_restart is not None:
+            o.gmres_restart = int(gmres_restart)
+        if gmres_maxit is not None:
+            o.gmres_maxit = int(gmres_maxit)
+        if guess is not None:
+            o.guess = _GUESS[guess]
         self.precision = o.precision
         self.R = int(R)
         self.nt = int(nt)
@@ -121,6 +173,23 @@ class Solver:
         """out: torch CUDA tensor (nsteps, R, ne) of the path dtype, or None to discard."""
         ptr = None if out is None else ctypes.c_void_p(out.data_ptr())
         _lib.check(_lib.load().tdcfie_step(self._h, int(nsteps), ptr), self._h)
+
+    def step_y(self, nsteps: int, out=None, y_out=None):
+        """step() that also writes y_n (nsteps, R, ne) of the path dtype to y_out."""
+        ptr = None if out is None else ctypes.c_void_p(out.data_ptr())
+        yp = None if y_out is None else ctypes.c_void_p(y_out.data_ptr())
+        _lib.check(_lib.load().tdcfie_step_y(self._h, int(nsteps), ptr, yp), self._h)
+
+    def gmres_stats(self):
+        v = [ctypes.c_int64() for _ in range(4)]
+        _lib.check(_lib.load().tdcfie_gmres_stats(self._h, *(ctypes.byref(x) for x in v)), self._h)
+        return dict(zip(("iterations", "steps", "max_per_step", "not_converged"), (x.value for x in v)))
+
+    def mlp_load(self, params):
+        """Load 4801 learned-guess parameters (array-like, float32) into the march."""
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+        assert a.size == _lib.MLP_NPARAM
+        _lib.check(_lib.load().tdcfie_mlp_load(self._h, _lib._ptr(a)), self._h)
 
     def march(self, pw: dict, out=None, out_on_host: bool = False):
         p = self._pw(pw)

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libtdcfie.so")
 FP64, FP32, BF16X3, FP16X3 = 0, 1, 2, 3
 SOLVE_DIRECT, SOLVE_GMRES = 0, 1
 GUESS_ZERO, GUESS_PREV, GUESS_MLP = 0, 1, 2
+MLP_NPARAM = 4801
 STATUS = {0: "OK", -1: "E_ARG", -2: "E_MESH", -3: "E_OOM", -4: "E_CUDA", -5: "E_NOCONV", -6: "E_TIMEOUT",
           -7: "E_NONFINITE", -8: "E_STATE", -9: "E_UNSUPPORTED"}
 
@@ -47,6 +48,8 @@ SIGNATURES = [
     ("tdcfie_set_excitation", _I, [_P, _P]),
     ("tdcfie_step", _I, [_P, _I64, _P]),
     ("tdcfie_march", _I, [_P, _P, _P, _I]),
+    ("tdcfie_step_y", _I, [_P, _I64, _P, _P]),
+    ("tdcfie_gmres_stats", _I, [_P, _P, _P, _P, _P]),
     ("tdcfie_info", _I, [_P, _P, _P, _P, _P, _P, _P]),
     ("tdcfie_topology", _I, [_P, _P, _P, _P]),
     ("tdcfie_bc_table", _I, [_P, _P, _P, _P, _P, _P, _P]),
@@ -55,6 +58,10 @@ SIGNATURES = [
     ("tdcfie_assembly_timing", _I, [_P, _P]),
     ("tdcfie_block_gemv", _I, [_I, _P, _I64, _I64, _P, _I64, _P, _P]),
     ("tdcfie_block_gemv_noalloc", _I, [_I, _P, _I64, _I64, _P, _I64, _P, _P]),
+    ("tdcfie_mlp_grad", _I, [_P, _P, _P, _I64, _P, _P, _P]),
+    ("tdcfie_mlp_train", _I, [_P, _P, _P, _I64, _I, _I64, ctypes.c_float, ctypes.c_uint64, _P, _P]),
+    ("tdcfie_mlp_predict", _I, [_P, _P, _I64, _P, _P]),
+    ("tdcfie_mlp_load", _I, [_P, _P]),
     ("tdcfie_destroy", _I, [_P]),
     ("tdcfie_last_error", ctypes.c_char_p, [_P]),
 ]

@@ -64,7 +64,13 @@ extern "C" tdcfie_status tdcfie_create(const double* vertices, int64_t nv, const
         return fail(nullptr, TDCFIE_E_UNSUPPORTED, "the tensor-core paths march exactly 64 right-hand sides");
     if (!tensor && o.max_rhs > 8)
         return fail(nullptr, TDCFIE_E_UNSUPPORTED, "FP64/FP32 paths march at most 8 right-hand sides together");
-    if (o.solver != TDCFIE_SOLVE_DIRECT) return fail(nullptr, TDCFIE_E_UNSUPPORTED, "only the direct solver is built");
+    if (o.solver != TDCFIE_SOLVE_DIRECT && o.solver != TDCFIE_SOLVE_GMRES)
+        return fail(nullptr, TDCFIE_E_ARG, "bad solver");
+    if (o.solver == TDCFIE_SOLVE_GMRES && tensor)
+        return fail(nullptr, TDCFIE_E_UNSUPPORTED, "GMRES runs on the FP64 and FP32 paths");
+    if (o.solver == TDCFIE_SOLVE_GMRES && !(o.gmres_tol > 0.0 && o.gmres_tol < 1.0))
+        return fail(nullptr, TDCFIE_E_ARG, "gmres_tol must be in (0, 1)");
+    if (o.guess < TDCFIE_GUESS_ZERO || o.guess > TDCFIE_GUESS_MLP) return fail(nullptr, TDCFIE_E_ARG, "bad guess");
     tdcfie_t h = new tdcfie_s();
     h->opts = o;
     h->R = o.max_rhs;
@@ -203,6 +209,29 @@ extern "C" tdcfie_status tdcfie_step(tdcfie_t h, int64_t nsteps, void* out) {
     if (nsteps < 0) return fail(h, TDCFIE_E_ARG, "nsteps < 0");
     if (nsteps == 0) return TDCFIE_OK;
     return plan_step(h, nsteps, out);
+}
+
+extern "C" tdcfie_status tdcfie_step_y(tdcfie_t h, int64_t nsteps, void* currents_out, void* y_out) {
+    if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
+    if (!h->excited) return fail(h, TDCFIE_E_STATE, "call tdcfie_set_excitation first");
+    if (nsteps < 0) return fail(h, TDCFIE_E_ARG, "nsteps < 0");
+    if (h->opts.precision == TDCFIE_BF16X3 || h->opts.precision == TDCFIE_FP16X3)
+        return fail(h, TDCFIE_E_UNSUPPORTED, "y output is built for the FP64 and FP32 paths");
+    if (nsteps == 0) return TDCFIE_OK;
+    return plan_step(h, nsteps, currents_out, y_out);
+}
+
+extern "C" tdcfie_status tdcfie_gmres_stats(tdcfie_t h, int64_t* inner_iterations, int64_t* steps,
+                                            int64_t* max_per_step, int64_t* not_converged) {
+    if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
+    long long v[5] = {0, 0, 0, 0, 0};
+    tdcfie_status st = plan_gmres_stats(h, v);
+    if (st != TDCFIE_OK) return st;
+    if (inner_iterations) *inner_iterations = v[0];
+    if (steps) *steps = v[1];
+    if (max_per_step) *max_per_step = v[2];
+    if (not_converged) *not_converged = v[4];
+    return TDCFIE_OK;
 }
 
 extern "C" tdcfie_status tdcfie_march(tdcfie_t h, const tdcfie_plane_waves* exc, void* out, int out_on_host) {

@@ -1,0 +1,24 @@
+// Restarted mixed-precision GMRES on T_0 (per-step solve of the MOT recurrence).
+#pragma once
+#include "internal.h"
+
+namespace tdc {
+struct StepPlan;
+struct GmresPlan;
+cudaError_t build_gmres(tdcfie_t h, StepPlan* p);
+void destroy_gmres(GmresPlan* g);
+cudaError_t reset_gmres_stats(GmresPlan* g);
+cudaError_t gmres_stats(GmresPlan* g, long long* out5);
+// b: right-hand side (path type, R x ne); learned: learned guess buffer (or nullptr); T0p: T_0 in the
+// path precision; the solution goes to ring slot n % ring.
+template <typename T>
+void launch_gmres(tdcfie_t h, StepPlan* p, const T* b, const T* learned, const T* T0p, T* ringbuf, cudaStream_t s);
+
+// Learned initial guess (mlp.cu): FP16 weights on the device, filled into p->guessbuf each step.
+struct MlpState;
+cudaError_t build_mlp(StepPlan* p);
+void destroy_mlp(MlpState* m);
+cudaError_t mlp_load(StepPlan* p, const float* host_params, cudaStream_t s);
+template <typename T>
+void launch_mlp_guess(StepPlan* p, cudaStream_t s);
+}  // namespace tdc

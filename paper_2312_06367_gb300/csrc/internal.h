@@ -89,6 +89,7 @@ struct Ctl {              // device-resident step state read by every kernel of 
     int status;           // 0 ok, else a tdcfie_status recorded with bad_step
     int64_t bad_step;
     int timeout;          // set by a device-side bounded wait that ran out
+    void* yout;           // optional y_n output of this call (nullptr: none)
 };
 }  // namespace tdc
 
@@ -130,5 +131,6 @@ tdcfie_status cuda_fail(tdcfie_t h, cudaError_t e, const char* where);
 tdcfie_status build_plan(tdcfie_t h);
 void free_plan(tdcfie_t h);
 tdcfie_status plan_reset(tdcfie_t h);
-tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out);
+tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout = nullptr);
+tdcfie_status plan_gmres_stats(tdcfie_t h, long long* out5);
 }  // namespace tdc

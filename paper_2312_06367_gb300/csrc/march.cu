@@ -18,6 +18,7 @@
 #include <string>
 
 #include "internal.h"
+#include "gmres.h"
 #include "plan.h"
 #include "umma.h"
 
@@ -164,6 +165,10 @@ __global__ void k_project_out(DevMesh m, int R, int ring, Ctl* ctl, const T* __r
         T* o = reinterpret_cast<T*>(ctl->out);
         o[((n - ctl->n0) * R + r) * (int64_t)m.ne + e] = val;
     }
+    if (ctl->yout) {
+        T* o = reinterpret_cast<T*>(ctl->yout);
+        o[((n - ctl->n0) * R + r) * (int64_t)m.ne + e] = yn[e];
+    }
 }
 
 __global__ void k_advance(Ctl* ctl) { ctl->n += 1; }
@@ -187,7 +192,11 @@ static void launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
     if (R == 1) HIST(1); else if (R <= 4) HIST(4); else HIST(8);
     k_reduce<T><<<(ne * R + tb - 1) / tb, tb, 0, s>>>((const T*)p.partial, p.nblk, ne, R, (T*)p.b);
     cudaEventRecordWithFlags(p.evB, s, cudaEventRecordExternal);
-    if (R == 1) APPLY(1, p.t0inv, ne, ne, p.b, p.ringbuf, p.ring);
+    p.launches_per_step = 0;
+    if (p.mlp) launch_mlp_guess<T>(&p, s);
+    if (p.gm) {
+        launch_gmres<T>(h, &p, (const T*)p.b, (const T*)p.guessbuf, (const T*)p.t0mat, (T*)p.ringbuf, s);
+    } else if (R == 1) APPLY(1, p.t0inv, ne, ne, p.b, p.ringbuf, p.ring);
     else if (R <= 4) APPLY(4, p.t0inv, ne, ne, p.b, p.ringbuf, p.ring);
     else APPLY(8, p.t0inv, ne, ne, p.b, p.ringbuf, p.ring);
     k_project_in<T><<<(p.nc * R + tb - 1) / tb, tb, 0, s>>>(m, R, p.ring, p.ctl, (const T*)p.ringbuf, h->dtt, (T*)p.z);
@@ -198,7 +207,15 @@ static void launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
     k_advance<<<1, 1, 0, s>>>(p.ctl);
 #undef HIST
 #undef APPLY
-    p.launches_per_step = 8;
+    p.launches_per_step += 8 - (p.gm ? 1 : 0);
+}
+
+tdcfie_status plan_gmres_stats(tdcfie_t h, long long* out5) {
+    StepPlan* p = h->plan;
+    if (!p || !p->gm) return fail(h, TDCFIE_E_STATE, "GMRES solver not active on this handle");
+    const cudaError_t e = gmres_stats(p->gm, out5);
+    if (e != cudaSuccess) return cuda_fail(h, e, "gmres_stats");
+    return TDCFIE_OK;
 }
 
 // host wrappers used by the tensor-core step (umma.cu)
@@ -229,6 +246,10 @@ void free_plan(tdcfie_t h) {
     if (p->ev1) cudaEventDestroy(p->ev1);
     if (p->ev2) cudaEventDestroy(p->ev2);
     if (p->gemm) destroy_bf16x3(p->gemm);
+    if (p->gm) destroy_gmres(p->gm);
+    if (p->mlp) destroy_mlp(p->mlp);
+    if (p->t0mat) cudaFree(p->t0mat);
+    if (p->guessbuf) cudaFree(p->guessbuf);
     if (p->evA) cudaEventDestroy(p->evA);
     if (p->evB) cudaEventDestroy(p->evB);
     for (auto e : p->hA) cudaEventDestroy(e);
@@ -367,6 +388,17 @@ tdcfie_status build_plan(tdcfie_t h) {
             to_path(s, p->prec, tmp, (char*)p->blocks + es * (1 + k) * ne * ne, ne * ne);
         }
         to_path(s, p->prec, h->T0inv, p->t0inv, ne * ne);
+        if (h->opts.solver == TDCFIE_SOLVE_GMRES) {
+            CK(cudaMalloc(&p->t0mat, es * ne * ne));
+            to_path(s, p->prec, h->T, p->t0mat, ne * ne);
+            CK(cudaMalloc(&p->guessbuf, es * R * ne));
+            CK(cudaMemset(p->guessbuf, 0, es * R * ne));
+            CK(build_gmres(h, p));
+            if (h->opts.guess == TDCFIE_GUESS_MLP) {
+                if (p->ring < 8) return fail(h, TDCFIE_E_UNSUPPORTED, "the learned guess needs K - 1 >= 8 stored steps");
+                CK(build_mlp(p));
+            }
+        }
         to_path(s, p->prec, h->PinvS, p->pinv, nc * nc);
         CK(cudaStreamSynchronize(s));
         cudaFree(tmp);
@@ -383,7 +415,8 @@ tdcfie_status build_plan(tdcfie_t h) {
 tdcfie_status plan_reset(tdcfie_t h) {
     StepPlan* p = h->plan;
     cudaStream_t s = h->stream;
-    Ctl c{1, 1, nullptr, 0, 0, 0};
+    Ctl c{1, 1, nullptr, 0, 0, 0, nullptr};
+    if (p->gm) CK(reset_gmres_stats(p->gm));
     CK(cudaMemcpyAsync(p->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(p->ringbuf, 0, p->esz * p->ring * p->R * p->ne, s));
     if (p->gemm) CK(reset_bf16x3(p->gemm, p->ring, s));
@@ -391,7 +424,7 @@ tdcfie_status plan_reset(tdcfie_t h) {
     return TDCFIE_OK;
 }
 
-tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out) {
+tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout) {
     StepPlan* p = h->plan;
     cudaStream_t s = h->stream;
     if (h->own_stream) {
@@ -436,6 +469,7 @@ tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out) {
     CK(cudaStreamSynchronize(s));
     c.n0 = c.n;
     c.out = out;
+    c.yout = yout;
     CK(cudaMemcpyAsync(p->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(p->ev0, s));
     for (int64_t i = 0; i < nsteps; ++i) {

@@ -6,6 +6,8 @@
 
 namespace tdc {
 struct Bf16x3Gemm;
+struct GmresPlan;
+struct MlpState;
 
 struct StepPlan {
     int prec = TDCFIE_FP64;
@@ -13,6 +15,10 @@ struct StepPlan {
     size_t esz = 8;
     void* blocks = nullptr;      // nblk x ne x ne (path precision): -A, alpha L2, -T_1 .. -T_{K-1}
     void* t0inv = nullptr;       // ne x ne
+    void* t0mat = nullptr;       // ne x ne, T_0 itself (GMRES matvec)
+    void* guessbuf = nullptr;    // R x ne learned initial guess
+    GmresPlan* gm = nullptr;
+    MlpState* mlp = nullptr;     // learned-guess network (GMRES with TDCFIE_GUESS_MLP)
     void* pinv = nullptr;        // nc x nc
     void* E = nullptr;           // R x ne  (e_n)
     void* Hv = nullptr;          // R x ne  (h_n)
