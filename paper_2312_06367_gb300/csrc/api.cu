@@ -224,7 +224,7 @@ extern "C" tdcfie_status tdcfie_step_y(tdcfie_t h, int64_t nsteps, void* current
 extern "C" tdcfie_status tdcfie_gmres_stats(tdcfie_t h, int64_t* inner_iterations, int64_t* steps,
                                             int64_t* max_per_step, int64_t* not_converged) {
     if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
-    long long v[5] = {0, 0, 0, 0, 0};
+    long long v[6] = {0, 0, 0, 0, 0, 0};
     tdcfie_status st = plan_gmres_stats(h, v);
     if (st != TDCFIE_OK) return st;
     if (inner_iterations) *inner_iterations = v[0];

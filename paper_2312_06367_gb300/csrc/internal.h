@@ -132,5 +132,5 @@ tdcfie_status build_plan(tdcfie_t h);
 void free_plan(tdcfie_t h);
 tdcfie_status plan_reset(tdcfie_t h);
 tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout = nullptr);
-tdcfie_status plan_gmres_stats(tdcfie_t h, long long* out5);
+tdcfie_status plan_gmres_stats(tdcfie_t h, long long* out6);
 }  // namespace tdc

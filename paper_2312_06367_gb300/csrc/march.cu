@@ -177,7 +177,7 @@ __global__ void k_advance(Ctl* ctl) { ctl->n += 1; }
 static size_t esize(int prec) { return prec == TDCFIE_FP64 ? 8 : 4; }
 
 template <typename T>
-static void launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
+static cudaError_t launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
     const tdc::DevMesh& m = h->dm;
     const int R = p.R, ne = p.ne;
     const int tb = 256;
@@ -195,7 +195,9 @@ static void launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
     p.launches_per_step = 0;
     if (p.mlp) launch_mlp_guess<T>(&p, s);
     if (p.gm) {
-        launch_gmres<T>(h, &p, (const T*)p.b, (const T*)p.guessbuf, (const T*)p.t0mat, (T*)p.ringbuf, s);
+        const cudaError_t e = launch_gmres<T>(h, &p, (const T*)p.b, (const T*)p.guessbuf, (const T*)p.t0mat,
+                                              (T*)p.ringbuf, s);
+        if (e != cudaSuccess) return e;
     } else if (R == 1) APPLY(1, p.t0inv, ne, ne, p.b, p.ringbuf, p.ring);
     else if (R <= 4) APPLY(4, p.t0inv, ne, ne, p.b, p.ringbuf, p.ring);
     else APPLY(8, p.t0inv, ne, ne, p.b, p.ringbuf, p.ring);
@@ -208,12 +210,13 @@ static void launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
 #undef HIST
 #undef APPLY
     p.launches_per_step += 8 - (p.gm ? 1 : 0);
+    return cudaGetLastError();
 }
 
-tdcfie_status plan_gmres_stats(tdcfie_t h, long long* out5) {
+tdcfie_status plan_gmres_stats(tdcfie_t h, long long* out6) {
     StepPlan* p = h->plan;
     if (!p || !p->gm) return fail(h, TDCFIE_E_STATE, "GMRES solver not active on this handle");
-    const cudaError_t e = gmres_stats(p->gm, out5);
+    const cudaError_t e = gmres_stats(p->gm, out6);
     if (e != cudaSuccess) return cuda_fail(h, e, "gmres_stats");
     return TDCFIE_OK;
 }
@@ -435,10 +438,16 @@ tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout) {
     if (!p->exec) {
         // capture one step
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        if (p->prec == TDCFIE_FP64) launch_step<double>(h, *p, s);
-        else if (p->prec == TDCFIE_FP32) launch_step<float>(h, *p, s);
+        cudaError_t ce = cudaSuccess;
+        if (p->prec == TDCFIE_FP64) ce = launch_step<double>(h, *p, s);
+        else if (p->prec == TDCFIE_FP32) ce = launch_step<float>(h, *p, s);
         else launch_step_bf16x3(h, p, s);
-        CK(cudaStreamEndCapture(s, &p->graph));
+        const cudaError_t ee = cudaStreamEndCapture(s, &p->graph);
+        if (ce != cudaSuccess) {
+            if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
+            return cuda_fail(h, ce, "capturing the step graph");
+        }
+        CK(ee);
         CK(cudaGraphInstantiate(&p->exec, p->graph, 0));
         size_t nn = 0;
         CK(cudaGraphGetNodes(p->graph, nullptr, &nn));
@@ -471,6 +480,8 @@ tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout) {
     c.out = out;
     c.yout = yout;
     CK(cudaMemcpyAsync(p->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    long long g0[6] = {0, 0, 0, 0, 0, 0}, g1[6] = {0, 0, 0, 0, 0, 0};
+    if (p->gm) CK(gmres_stats(p->gm, g0));
     CK(cudaEventRecord(p->ev0, s));
     for (int64_t i = 0; i < nsteps; ++i) {
         if (i < nev && p->nodeA && p->nodeB) {
@@ -493,6 +504,10 @@ tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout) {
     }
     h->last_hist_ms = cnt ? hs / cnt : 0.0;
     h->last_launches = nsteps * p->launches_per_step;
+    if (p->gm) {
+        CK(gmres_stats(p->gm, g1));
+        h->last_launches += (g1[5] - g0[5]) * gmres_body_launches();
+    }
     if (c.timeout)
         return fail(h, TDCFIE_E_TIMEOUT, "a bounded device-side wait ran out (tensor-core pipeline)");
     if (c.status != 0)
