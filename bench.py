@@ -35,6 +35,7 @@ def workload(name: str, precision: str | None = None):
         "torus864_fp32": workloads.torus864_fp32,
         "sphere7680_r64": workloads.sphere7680_r64,
         "sphere1920_r64": workloads.sphere1920_r64,
+        "ellipsoid12288": workloads.ellipsoid12288,
     }[name]()
     if precision:
         w["precision"] = precision
@@ -185,6 +186,130 @@ def run_reference(args, w):
     return 0
 
 
+def batched_vs_plain(s, w, host_out, batched_steps_s, stream, args):
+    """The plain GPU march of one incident wave (FP32 path, R = 1, same assembled blocks) against
+    the batched tensor-core march of all R waves: rates per wave-step and the currents of wave 0
+    over the same steps (rel-L2 of the two)."""
+    import numpy as np
+    import torch
+    R = int(w["pw"]["k"].shape[0])
+    nst = host_out.shape[0]
+    s.replan("fp32", 1)
+    one = {k: v[:1] for k, v in w["pw"].items()}
+    out1 = torch.empty((nst, 1, s.ne), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        s.march(one, out1)                       # warm-up pass (captures the step graph)
+        s.march(one, out1)
+        torch.cuda.synchronize()
+    plain = 1e3 / s.timing()["step_ms"]
+    a = out1[:, 0, :].double().cpu().numpy()
+    b = host_out[:, 0, :].astype(np.float64)
+    err = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    return {"plain": "FP32 history sum, R = 1 (one incident wave per march), same blocks",
+            "plain_steps_s": plain, "plain_wave_steps_s": plain, "batched_wave_steps_s": batched_steps_s * R,
+            "speedup_per_wave": batched_steps_s * R / plain, "steps_compared": nst,
+            "rel_l2_wave0_batched_vs_plain": err}
+
+
+def run_guess_study(args, w):
+    """The learned GMRES initial guess: trained on 7680-edge sphere trajectories, evaluated on the
+    12288-edge ellipsoid against zero and previous-step guesses and the direct T_0^-1 solve (the
+    plain GPU march), all on one assembled handle at FP32 with GMRES tol 1e-8."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2312_06367_gb300 import Solver, mlp_samples, mlp_train
+    from synth import workloads
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    info = {}
+    # 1. training trajectories (plain FP32 direct march of 8 waves) and samples, on the GPU
+    tw = workloads.sphere7680_train8()
+    t0 = time.time()
+    st = Solver(tw["V"], tw["F"], dt=tw["dt"], nt=tw["Nt"], precision="fp32", R=8, stream=stream.cuda_stream).assemble()
+    info["train_assemble_s"] = round(time.time() - t0, 1)
+    y = torch.empty((tw["Nt"], 8, st.ne), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        st.set_excitation(tw["pw"])
+        st.step_y(tw["Nt"], None, y)
+        X, Y = mlp_samples(y)
+        torch.cuda.synchronize()
+    st.close()
+    del y
+    # 2. training (Adam, GPU kernels); initial parameters: uniform(+-1/sqrt(fan_in)), zero biases
+    rng = np.random.default_rng(2312063672)
+    parts = []
+    for fan_in, n_w, n_b in ((8, 64 * 8, 64), (64, 64 * 64, 64), (64, 64, 1)):
+        lim = 1.0 / np.sqrt(fan_in)
+        parts += [rng.uniform(-lim, lim, n_w), np.zeros(n_b)]
+    params = torch.tensor(np.concatenate(parts), dtype=torch.float32, device="cuda")
+    t0 = time.time()
+    with torch.cuda.stream(stream):
+        hist = mlp_train(params, X, Y, epochs=args.train_epochs, batch=4096, lr=1e-3, seed=7)
+    torch.cuda.synchronize()
+    info.update(train_samples=int(X.shape[0]), train_epochs=args.train_epochs, train_s=round(time.time() - t0, 2),
+                train_loss_first=float(hist[0]), train_loss_last=float(hist[-1]))
+    del X, Y
+    torch.cuda.empty_cache()                      # the evaluation assembly needs most of the HBM
+    # 3. evaluation handle
+    t0 = time.time()
+    s = Solver(w["V"], w["F"], dt=w["dt"], nt=w["Nt"], alpha=w["alpha"], precision="fp32", R=1,
+               stream=stream.cuda_stream, solver="gmres", guess="zero", gmres_tol=w["gmres_tol"]).assemble()
+    t_asm = time.time() - t0
+    s.mlp_load(params.cpu().numpy())
+    nt = w["Nt"]
+    outs, rows = {}, {}
+    for mode in ("direct", "zero", "prev", "mlp"):
+        if mode == "direct":
+            s.set_solver("direct")
+        else:
+            s.set_solver("gmres", mode, w["gmres_tol"])
+        out = torch.empty((nt, 1, s.ne), dtype=torch.float32, device="cuda")
+        with torch.cuda.stream(stream):
+            s.set_excitation(w["pw"])
+            s.step(args.warmup)                   # warm-up: captures the step graph
+            torch.cuda.synchronize()
+            with Clocks(local) as clk:
+                s.march(w["pw"], out)
+                torch.cuda.synchronize()
+        tm = s.timing()
+        row = {"steps_s": 1e3 / tm["step_ms"], "ms_per_step": tm["step_ms"], "history_ms": tm["history_ms"],
+               "launches": tm["launches"], "clocks": clk.summary()}
+        if mode != "direct":
+            row.update(s.gmres_stats())
+        rows[mode] = row
+        outs[mode] = out[:, 0, :].double()
+    ref = outs["direct"]
+    for mode in rows:
+        rows[mode]["rel_l2_vs_direct"] = float(torch.linalg.norm(outs[mode] - ref) / torch.linalg.norm(ref))
+    m = rows["mlp"]
+    pk = peaks()
+    hb = s.timing()["history_bytes"]
+    line = {
+        "metric": METRIC, "value": m["steps_s"], "unit": "steps/s", "n_gpus": 1, "steps": nt, "warmup": args.warmup,
+        "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["name"], "edges": s.ne, "triangles": s.nc, "R": 1, "K": s.K, "dt": w["dt"],
+                   "solver": "gmres", "guess": "mlp", "gmres_tol": w["gmres_tol"], "assemble_s": round(t_asm, 1),
+                   "cache": "inputs larger than L2"},
+        "gpu_launches": int(m["launches"]),
+        "roofline": {"bound": "hbm", "achieved": hb / (m["history_ms"] / 1e3) / 1e9 if m["history_ms"] else None,
+                     "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": (hb / (m["history_ms"] / 1e3) / 1e9 / pk["hbm_gbs"]) if m["history_ms"] else None,
+                     "traffic": None, "kernel": "history sum (k_history + k_reduce)",
+                     "algorithmic_bytes_per_launch": hb},
+        "guess_study": rows, "training": info,
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
 def run_ours(args, w):
     import numpy as np
     import torch
@@ -262,6 +387,9 @@ def run_ours(args, w):
     barrier()
     e1 = time.perf_counter()
     e2e = ws * args.steps / (e1 - e0)
+    batched = None
+    if R > 1 and prec in ("bf16x3", "fp16x3"):
+        batched = batched_vs_plain(s, w, host_out, value / ws, stream, args)
     # roofline of the dominant kernel (history sum: streams every history and right-hand-side block)
     pk = peaks()
     h_ms = statistics.mean(hist_ms) if hist_ms and hist_ms[0] > 0 else None
@@ -293,6 +421,8 @@ def run_ours(args, w):
                      "peak_source": "measured" if not pk.get("fallback") else "fallback"},
         "clocks": clk.summary(),
     }
+    if batched:
+        line["batched_vs_plain"] = batched
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n, t_casm = cpu_oracle_rate(w, 4 * args.steps + 50)
         sample = (f"{n} march steps of the same workload (assembly {t_casm:.1f} s untimed)" if t_casm is not None else
@@ -317,11 +447,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, help="override the workload's path precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--train-epochs", type=int, default=4, help="learned-guess training passes (ellipsoid12288)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     w = workload(args.workload, args.precision)
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.workload == "ellipsoid12288":
+        return run_guess_study(args, w)
     return run_ours(args, w)
 
 

@@ -153,10 +153,31 @@ tdcfie_status tdcfie_mlp_train(float* params, const float* X, const float* Y, in
  * arithmetic; DEVICE pointers. */
 tdcfie_status tdcfie_mlp_predict(const float* params, const float* X, int64_t n, float* out, void* stream);
 
-/* Load network parameters (HOST, 4801 floats) into a handle assembled with solver GMRES and
- * guess TDCFIE_GUESS_MLP (which needs K - 1 >= 8).  Synchronous.  Until loaded the weights are zero
- * and so is the guess. */
+/* Training samples from a stored march: y (DEVICE, nt x R x N_E, float64 for precision
+ * TDCFIE_FP64 or float32 for TDCFIE_FP32, as written by tdcfie_step_y).  For t = 8 .. nt-1 (0-based
+ * rows of y) and every r, m, sample s = ((t - 8) R + r) N_E + m gets X[s] = (y[t-1] .. y[t-8])_{r,m} / sc
+ * and Y[s] = y[t]_{r,m} / sc, sc = RMS over edges of y[t-1]_r (1 if zero), FP32 arithmetic: the
+ * features the march evaluates before each GMRES solve.  X (DEVICE) holds (nt - 8) R N_E x 8 floats,
+ * Y (nt - 8) R N_E.  Needs nt >= 9. */
+tdcfie_status tdcfie_mlp_samples(int precision, const void* y, int64_t nt, int64_t R, int64_t ne, float* X, float* Y,
+                                 void* stream);
+
+/* Load network parameters (HOST, 4801 floats) into an assembled handle (K - 1 >= 8); they are used
+ * while the solver is GMRES with guess TDCFIE_GUESS_MLP.  Synchronous.  Until loaded the weights are
+ * zero and so is the guess. */
 tdcfie_status tdcfie_mlp_load(tdcfie_t h, const float* params);
+
+/* Rebuild the step plan of an assembled handle for another path precision and number of
+ * right-hand sides (same limits as tdcfie_create) without assembling again: the FP64 blocks are
+ * converted anew.  FP64 needs a handle assembled with precision FP64 (the reduced paths form the
+ * T_k products in FP32).  The excitation must be set again; a tensor-core plan uses the direct
+ * solve. */
+tdcfie_status tdcfie_replan(tdcfie_t h, int precision, int64_t max_rhs);
+
+/* Change the per-step solve of an assembled handle (FP64 and FP32 paths for GMRES): solver, initial
+ * guess and GMRES tolerance as in tdcfie_opts.  The march state is kept; the step graph is captured
+ * again at the next step.  GMRES statistics keep accumulating until the next set_excitation. */
+tdcfie_status tdcfie_set_solver(tdcfie_t h, int solver, int guess, double gmres_tol);
 
 /* Whole march: set_excitation, then nt steps into currents_out.  out_on_host != 0: currents_out is a
  * HOST buffer (pinned or pageable) and the device-to-host copy is part of the call. */

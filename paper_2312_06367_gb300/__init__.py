@@ -13,7 +13,8 @@ import numpy as np
 from . import _lib
 from ._lib import BF16X3, FP16X3, FP32, FP64, TdcfieError  # noqa: F401
 
-__all__ = ["Solver", "block_gemv", "block_gemv_noalloc", "mlp_grad", "mlp_train", "mlp_predict", "FP64", "FP32", "BF16X3", "FP16X3", "TdcfieError"]
+__all__ = ["Solver", "block_gemv", "block_gemv_noalloc", "mlp_grad", "mlp_train", "mlp_predict", "mlp_samples",
+           "FP64", "FP32", "BF16X3", "FP16X3", "TdcfieError"]
 
 
 def block_gemv(blocks, x, out=None, stream=None):
@@ -84,6 +85,19 @@ def mlp_predict(params, X, stream=None):
     _lib.check(_lib.load().tdcfie_mlp_predict(_vp(params), _vp(X), X.shape[0], _vp(out),
                                               ctypes.c_void_p(_stream(params, stream))))
     return out
+
+
+def mlp_samples(y, stream=None):
+    """(X, Y) training samples of a stored march y (nt, R, ne) through tdcfie_mlp_samples."""
+    import torch
+    nt, R, ne = y.shape
+    ns = (nt - 8) * R * ne
+    X = torch.empty((ns, 8), dtype=torch.float32, device=y.device)
+    Y = torch.empty(ns, dtype=torch.float32, device=y.device)
+    prec = FP64 if y.dtype == torch.float64 else FP32
+    _lib.check(_lib.load().tdcfie_mlp_samples(prec, _vp(y), nt, R, ne, _vp(X), _vp(Y),
+                                              ctypes.c_void_p(_stream(y, stream))))
+    return X, Y
 
 
 _SOLVE = {"direct": _lib.SOLVE_DIRECT, "gmres": _lib.SOLVE_GMRES}
@@ -184,6 +198,16 @@ class Solver:
         v = [ctypes.c_int64() for _ in range(4)]
         _lib.check(_lib.load().tdcfie_gmres_stats(self._h, *(ctypes.byref(x) for x in v)), self._h)
         return dict(zip(("iterations", "steps", "max_per_step", "not_converged"), (x.value for x in v)))
+
+    def replan(self, precision: str, R: int):
+        """Rebuild the step plan for another path precision / number of waves (tdcfie_replan)."""
+        o = _PREC[precision] if isinstance(precision, str) else int(precision)
+        _lib.check(_lib.load().tdcfie_replan(self._h, o, int(R)), self._h)
+        self.precision, self.R = o, int(R)
+
+    def set_solver(self, solver: str = "gmres", guess: str = "prev", gmres_tol: float = 1e-8):
+        """Switch the per-step solve of the assembled handle (tdcfie_set_solver)."""
+        _lib.check(_lib.load().tdcfie_set_solver(self._h, _SOLVE[solver], _GUESS[guess], float(gmres_tol)), self._h)
 
     def mlp_load(self, params):
         """Load 4801 learned-guess parameters (array-like, float32) into the march."""

@@ -61,7 +61,10 @@ SIGNATURES = [
     ("tdcfie_mlp_grad", _I, [_P, _P, _P, _I64, _P, _P, _P]),
     ("tdcfie_mlp_train", _I, [_P, _P, _P, _I64, _I, _I64, ctypes.c_float, ctypes.c_uint64, _P, _P]),
     ("tdcfie_mlp_predict", _I, [_P, _P, _I64, _P, _P]),
+    ("tdcfie_mlp_samples", _I, [_I, _P, _I64, _I64, _I64, _P, _P, _P]),
     ("tdcfie_mlp_load", _I, [_P, _P]),
+    ("tdcfie_set_solver", _I, [_P, _I, _I, _D]),
+    ("tdcfie_replan", _I, [_P, _I, _I64]),
     ("tdcfie_destroy", _I, [_P]),
     ("tdcfie_last_error", ctypes.c_char_p, [_P]),
 ]

@@ -176,6 +176,7 @@ extern "C" tdcfie_status tdcfie_assemble(tdcfie_t h) {
     if (st != TDCFIE_OK) return st;
     h->asm_s[4] = now_s() - t0;
     h->assembled = true;
+    h->formed_fp64 = h->opts.precision == TDCFIE_FP64;
     t0 = now_s();
     st = build_plan(h);
     if (st != TDCFIE_OK) return st;
@@ -232,6 +233,37 @@ extern "C" tdcfie_status tdcfie_gmres_stats(tdcfie_t h, int64_t* inner_iteration
     if (max_per_step) *max_per_step = v[2];
     if (not_converged) *not_converged = v[4];
     return TDCFIE_OK;
+}
+
+extern "C" tdcfie_status tdcfie_replan(tdcfie_t h, int precision, int64_t max_rhs) {
+    if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
+    if (!h->assembled) return fail(h, TDCFIE_E_STATE, "call tdcfie_assemble first");
+    if (precision < TDCFIE_FP64 || precision > TDCFIE_FP16X3) return fail(h, TDCFIE_E_ARG, "bad precision");
+    const bool tensor = precision == TDCFIE_BF16X3 || precision == TDCFIE_FP16X3;
+    if (max_rhs < 1 || (tensor && max_rhs != 64) || (!tensor && max_rhs > 8))
+        return fail(h, TDCFIE_E_UNSUPPORTED, "R must be 64 on the tensor-core paths and 1..8 on FP64/FP32");
+    if (precision == TDCFIE_FP64 && !h->formed_fp64)
+        return fail(h, TDCFIE_E_UNSUPPORTED, "the FP64 path needs blocks formed in FP64 (assemble with precision FP64)");
+    if (tensor && h->opts.solver == TDCFIE_SOLVE_GMRES) h->opts.solver = TDCFIE_SOLVE_DIRECT;
+    h->opts.precision = precision;
+    h->opts.max_rhs = max_rhs;
+    if (h->R != max_rhs && h->dexc) {
+        cudaFree(h->dexc);
+        h->dexc = nullptr;
+    }
+    h->R = max_rhs;
+    h->excited = false;
+    return build_plan(h);
+}
+
+extern "C" tdcfie_status tdcfie_set_solver(tdcfie_t h, int solver, int guess, double gmres_tol) {
+    if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
+    if (!h->assembled || !h->plan) return fail(h, TDCFIE_E_STATE, "call tdcfie_assemble first");
+    if (solver != TDCFIE_SOLVE_DIRECT && solver != TDCFIE_SOLVE_GMRES) return fail(h, TDCFIE_E_ARG, "bad solver");
+    if (guess < TDCFIE_GUESS_ZERO || guess > TDCFIE_GUESS_MLP) return fail(h, TDCFIE_E_ARG, "bad guess");
+    if (solver == TDCFIE_SOLVE_GMRES && !(gmres_tol > 0.0 && gmres_tol < 1.0))
+        return fail(h, TDCFIE_E_ARG, "gmres_tol must be in (0, 1)");
+    return plan_set_solver(h, solver, guess, gmres_tol);
 }
 
 extern "C" tdcfie_status tdcfie_march(tdcfie_t h, const tdcfie_plane_waves* exc, void* out, int out_on_host) {

@@ -337,6 +337,8 @@ cudaError_t build_gmres(tdcfie_t h, StepPlan* p) {
     return cudaMemset(d.stats, 0, sizeof(unsigned long long) * NSTATS);
 }
 
+void gmres_set_tol(GmresPlan* g, double tol) { g->d.tol = tol; }
+
 cudaError_t reset_gmres_stats(GmresPlan* g) { return cudaMemset(g->d.stats, 0, sizeof(unsigned long long) * NSTATS); }
 
 cudaError_t gmres_stats(GmresPlan* g, long long* out6) {

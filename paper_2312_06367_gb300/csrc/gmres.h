@@ -8,6 +8,7 @@ struct GmresPlan;
 cudaError_t build_gmres(tdcfie_t h, StepPlan* p);
 void destroy_gmres(GmresPlan* g);
 cudaError_t reset_gmres_stats(GmresPlan* g);
+void gmres_set_tol(GmresPlan* g, double tol);
 // out6: Arnoldi iterations, steps, max per step, this step, solves not converged, loop passes
 cudaError_t gmres_stats(GmresPlan* g, long long* out6);
 int gmres_body_launches();

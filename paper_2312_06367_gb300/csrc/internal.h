@@ -104,6 +104,7 @@ struct tdcfie_s {
     int64_t nt = 0;
     int K = 0;
     bool assembled = false, excited = false;
+    bool formed_fp64 = false;   // T_k products formed in FP64 (opts.precision was FP64 at assembly)
     // device mesh
     void* dmesh_buf = nullptr;
     tdc::DevMesh dm{};
@@ -133,4 +134,5 @@ void free_plan(tdcfie_t h);
 tdcfie_status plan_reset(tdcfie_t h);
 tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout = nullptr);
 tdcfie_status plan_gmres_stats(tdcfie_t h, long long* out6);
+tdcfie_status plan_set_solver(tdcfie_t h, int solver, int guess, double tol);
 }  // namespace tdc

@@ -193,8 +193,8 @@ static cudaError_t launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
     k_reduce<T><<<(ne * R + tb - 1) / tb, tb, 0, s>>>((const T*)p.partial, p.nblk, ne, R, (T*)p.b);
     cudaEventRecordWithFlags(p.evB, s, cudaEventRecordExternal);
     p.launches_per_step = 0;
-    if (p.mlp) launch_mlp_guess<T>(&p, s);
-    if (p.gm) {
+    if (p.mlp_on) launch_mlp_guess<T>(&p, s);
+    if (p.gmres_on) {
         const cudaError_t e = launch_gmres<T>(h, &p, (const T*)p.b, (const T*)p.guessbuf, (const T*)p.t0mat,
                                               (T*)p.ringbuf, s);
         if (e != cudaSuccess) return e;
@@ -209,7 +209,7 @@ static cudaError_t launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
     k_advance<<<1, 1, 0, s>>>(p.ctl);
 #undef HIST
 #undef APPLY
-    p.launches_per_step += 8 - (p.gm ? 1 : 0);
+    p.launches_per_step += 8 - (p.gmres_on ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -391,17 +391,6 @@ tdcfie_status build_plan(tdcfie_t h) {
             to_path(s, p->prec, tmp, (char*)p->blocks + es * (1 + k) * ne * ne, ne * ne);
         }
         to_path(s, p->prec, h->T0inv, p->t0inv, ne * ne);
-        if (h->opts.solver == TDCFIE_SOLVE_GMRES) {
-            CK(cudaMalloc(&p->t0mat, es * ne * ne));
-            to_path(s, p->prec, h->T, p->t0mat, ne * ne);
-            CK(cudaMalloc(&p->guessbuf, es * R * ne));
-            CK(cudaMemset(p->guessbuf, 0, es * R * ne));
-            CK(build_gmres(h, p));
-            if (h->opts.guess == TDCFIE_GUESS_MLP) {
-                if (p->ring < 8) return fail(h, TDCFIE_E_UNSUPPORTED, "the learned guess needs K - 1 >= 8 stored steps");
-                CK(build_mlp(p));
-            }
-        }
         to_path(s, p->prec, h->PinvS, p->pinv, nc * nc);
         CK(cudaStreamSynchronize(s));
         cudaFree(tmp);
@@ -412,7 +401,46 @@ tdcfie_status build_plan(tdcfie_t h) {
     CK(cudaEventCreate(&p->evA));
     CK(cudaEventCreate(&p->evB));
     h->hist_bytes = (double)p->nblk * ne * ne * (p->prec == TDCFIE_FP64 ? 8.0 : 4.0);
+    if (h->opts.solver == TDCFIE_SOLVE_GMRES) {
+        const tdcfie_status st = plan_set_solver(h, h->opts.solver, h->opts.guess, h->opts.gmres_tol);
+        if (st != TDCFIE_OK) return st;
+    }
     return plan_reset(h);
+}
+
+// Select the per-step solve of an existing plan; GMRES state, T_0 in the path precision and the
+// learned-guess network are allocated on first use.  The step graph is captured again at the next
+// step.
+tdcfie_status plan_set_solver(tdcfie_t h, int solver, int guess, double tol) {
+    StepPlan* p = h->plan;
+    cudaStream_t s = h->stream;
+    const int64_t ne = p->ne, R = p->R;
+    const size_t es = p->esz;
+    if (solver == TDCFIE_SOLVE_GMRES && (p->prec == TDCFIE_BF16X3 || p->prec == TDCFIE_FP16X3))
+        return fail(h, TDCFIE_E_UNSUPPORTED, "GMRES runs on the FP64 and FP32 paths");
+    if (solver == TDCFIE_SOLVE_GMRES && guess == TDCFIE_GUESS_MLP && p->ring < 8)
+        return fail(h, TDCFIE_E_UNSUPPORTED, "the learned guess needs K - 1 >= 8 stored steps");
+    h->opts.solver = solver;
+    h->opts.guess = guess;
+    h->opts.gmres_tol = tol;
+    if (solver == TDCFIE_SOLVE_GMRES) {
+        if (!p->t0mat) {
+            CK(cudaMalloc(&p->t0mat, es * ne * ne));
+            to_path(s, p->prec, h->T, p->t0mat, ne * ne);
+            CK(cudaMalloc(&p->guessbuf, es * R * ne));
+            CK(cudaMemsetAsync(p->guessbuf, 0, es * R * ne, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        if (!p->gm) CK(build_gmres(h, p));
+        gmres_set_tol(p->gm, tol);
+        if (guess == TDCFIE_GUESS_MLP && !p->mlp) CK(build_mlp(p));
+    }
+    p->gmres_on = solver == TDCFIE_SOLVE_GMRES;
+    p->mlp_on = p->gmres_on && guess == TDCFIE_GUESS_MLP;
+    if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
+    if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
+    p->nodeA = p->nodeB = nullptr;
+    return TDCFIE_OK;
 }
 
 tdcfie_status plan_reset(tdcfie_t h) {

@@ -150,27 +150,52 @@ __global__ void k_mlp_predict(const __half* __restrict__ wh, const float* __rest
     out[s] = mlp_forward(P, x);
 }
 
-// s_r = RMS over edges of y_{n-1} (one block per right-hand side)
+// RMS over ne entries of one vector, FP32 accumulation; block of 256 threads, result to all threads
+// (1 for a zero vector).  Used both for the in-march guess and for training samples, so that the two
+// scale their features identically.
 template <typename T>
-__global__ void k_mlp_rms(const T* __restrict__ ringbuf, int ring, int R, int ne, const Ctl* ctl,
-                          float* __restrict__ scale) {
-    __shared__ float red[256];
-    const int r = blockIdx.x;
-    const int64_t n = ctl->n;
+__device__ float block_rms(const T* __restrict__ y, int ne, float* red) {
     float a = 0.f;
-    if (n > 1) {
-        const T* y = ringbuf + ((n - 1) % ring) * (int64_t)R * ne + (int64_t)r * ne;
+    if (y)
         for (int i = threadIdx.x; i < ne; i += blockDim.x) a += (float)y[i] * (float)y[i];
-    }
     red[threadIdx.x] = a;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const float s = sqrtf(red[0] / ne);
-        scale[r] = s > 0.f ? s : 1.f;
+    const float s = sqrtf(red[0] / ne);
+    __syncthreads();
+    return s > 0.f ? s : 1.f;
+}
+
+// s_r = RMS over edges of y_{n-1} (one block of 256 threads per right-hand side)
+template <typename T>
+__global__ void k_mlp_rms(const T* __restrict__ ringbuf, int ring, int R, int ne, const Ctl* ctl,
+                          float* __restrict__ scale) {
+    __shared__ float red[256];
+    const int r = blockIdx.x;
+    const int64_t n = ctl->n;
+    const T* y = n > 1 ? ringbuf + ((n - 1) % ring) * (int64_t)R * ne + (int64_t)r * ne : nullptr;
+    const float s = block_rms(y, ne, red);
+    if (threadIdx.x == 0) scale[r] = s;
+}
+
+// Training samples from a stored trajectory y (nt x R x ne, step-major): for t = 8 .. nt-1 the
+// sample ((t - 8) R + r) ne + m has X = (y[t-1] .. y[t-8])_{r,m} / s and Y = y[t]_{r,m} / s with
+// s = RMS_m y[t-1]_r.  One block of 256 threads per (t, r).
+template <typename T>
+__global__ void k_mlp_samples(const T* __restrict__ y, int R, int ne, float* __restrict__ X, float* __restrict__ Y) {
+    __shared__ float red[256];
+    const int64_t q = blockIdx.x;          // (t - 8) * R + r
+    const int r = (int)(q % R);
+    const int64_t t = q / R + 8;
+    auto at = [&](int64_t step) { return y + (step * R + r) * (int64_t)ne; };
+    const float s = block_rms(at(t - 1), ne, red);
+    for (int m = threadIdx.x; m < ne; m += blockDim.x) {
+        const int64_t o = q * ne + m;
+        for (int k = 1; k <= NIN; ++k) X[o * NIN + k - 1] = (float)at(t - k)[m] / s;
+        Y[o] = (float)at(t)[m] / s;
     }
 }
 
@@ -330,9 +355,30 @@ extern "C" tdcfie_status tdcfie_mlp_predict(const float* params, const float* X,
     return e == cudaSuccess ? TDCFIE_OK : cuda_fail(nullptr, e, "MLP predict launch");
 }
 
+extern "C" tdcfie_status tdcfie_mlp_samples(int precision, const void* y, int64_t nt, int64_t R, int64_t ne,
+                                            float* X, float* Y, void* stream) {
+    if (!y || !X || !Y) return fail(nullptr, TDCFIE_E_ARG, "NULL device pointer");
+    if (precision != TDCFIE_FP64 && precision != TDCFIE_FP32) return fail(nullptr, TDCFIE_E_ARG, "y is float64 or float32");
+    if (nt < 9 || R < 1 || ne < 1) return fail(nullptr, TDCFIE_E_ARG, "need nt >= 9, R >= 1, ne >= 1");
+    if (ne > INT32_MAX || (nt - 8) * R > INT32_MAX) return fail(nullptr, TDCFIE_E_ARG, "sizes out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned blocks = (unsigned)((nt - 8) * R);
+    if (precision == TDCFIE_FP64)
+        k_mlp_samples<double><<<blocks, 256, 0, s>>>((const double*)y, (int)R, (int)ne, X, Y);
+    else
+        k_mlp_samples<float><<<blocks, 256, 0, s>>>((const float*)y, (int)R, (int)ne, X, Y);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TDCFIE_OK : cuda_fail(nullptr, e, "MLP sample launch");
+}
+
 extern "C" tdcfie_status tdcfie_mlp_load(tdcfie_t h, const float* params) {
     if (!h || !params) return fail(h, TDCFIE_E_ARG, "NULL argument");
-    if (!h->plan || !h->plan->mlp) return fail(h, TDCFIE_E_STATE, "assemble with opts.guess = TDCFIE_GUESS_MLP first");
+    if (!h->plan) return fail(h, TDCFIE_E_STATE, "call tdcfie_assemble first");
+    if (h->plan->ring < 8) return fail(h, TDCFIE_E_UNSUPPORTED, "the learned guess needs K - 1 >= 8 stored steps");
+    if (!h->plan->mlp) {
+        const cudaError_t eb = build_mlp(h->plan);
+        if (eb != cudaSuccess) return cuda_fail(h, eb, "learned-guess state");
+    }
     const cudaError_t e = mlp_load(h->plan, params, h->stream);
     return e == cudaSuccess ? TDCFIE_OK : cuda_fail(h, e, "tdcfie_mlp_load");
 }

@@ -19,6 +19,8 @@ struct StepPlan {
     void* guessbuf = nullptr;    // R x ne learned initial guess
     GmresPlan* gm = nullptr;
     MlpState* mlp = nullptr;     // learned-guess network (GMRES with TDCFIE_GUESS_MLP)
+    bool gmres_on = false;       // per-step solve by GMRES (else the explicit T_0^-1)
+    bool mlp_on = false;         // learned guess evaluated each step
     void* pinv = nullptr;        // nc x nc
     void* E = nullptr;           // R x ne  (e_n)
     void* Hv = nullptr;          // R x ne  (h_n)

@@ -15,6 +15,8 @@ coupling alpha and the plane-wave batch.  Names state what they are:
                      same tensor-core kernels whose blocks (634 MB) still exceed the L2 cache.
   ellipsoid12288     octasphere level 5 scaled to semi-axes (2, 1, 0.5) (8192 tri / 12288 edges),
                      dt 0.1, 1500 steps, GMRES tol 1e-8 (learned initial guess).
+  sphere7680_train8  icosphere level 4, dt 0.1, 300 steps, 8 Fibonacci directions (seed 2312063671),
+                     sigma 2: trajectories that train the learned GMRES guess.
   batch32            32 seeded scatterers (spheres, ellipsoids, tori) of 480..12288 edges, dt 0.2,
                      1000 steps, one direction each.
 """
@@ -56,6 +58,14 @@ def ellipsoid12288():
     return dict(name="ellipsoid12288", V=V, F=F, dt=0.1, Nt=1500, alpha=1.0,
                 pw=excitation.single(t0=8.0, sigma=2.0), precision="fp32", solver="gmres",
                 gmres_tol=1e-8)
+
+
+def sphere7680_train8():
+    """Training trajectories for the learned GMRES guess: the 7680-edge sphere, dt 0.1, 8 Fibonacci
+    directions with seeded polarisations, the same pulse width as the ellipsoid evaluation."""
+    V, F = meshes.icosphere(4)
+    return dict(name="sphere7680_train8", V=V, F=F, dt=0.1, Nt=300, alpha=1.0,
+                pw=excitation.fibonacci_batch(8, seed=2312063671, t0=8.0, sigma=2.0), precision="fp32")
 
 
 def batch32(seed: int = 2312063675, n: int = 32):

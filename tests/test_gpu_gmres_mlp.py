@@ -182,3 +182,42 @@ def test_mlp_guess_in_march(case):
         assert st["not_converged"] == 0
         assert rel(out.cpu().numpy().transpose(0, 2, 1), case["j"]) < 1e-10
     print("GMRES iterations by initial guess", its)
+
+
+def test_mlp_samples_match_oracle_features(case):
+    """tdcfie_mlp_samples builds the same features and targets as the oracle's definition."""
+    import torch
+    from oracle import mlp
+    from paper_2312_06367_gb300 import mlp_samples
+    s, _, y = _march(case)                          # y (nt, ne, R), FP64
+    yt = torch.tensor(np.ascontiguousarray(y.transpose(0, 2, 1)), device="cuda")   # (nt, R, ne)
+    X, Y = mlp_samples(yt)
+    torch.cuda.synchronize()
+    R, ne = 3, s.ne
+    X = X.double().cpu().numpy().reshape(NT - 8, R, ne, 8)
+    Y = Y.double().cpu().numpy().reshape(NT - 8, R, ne)
+    for t in (8, 9, 20, NT - 1):
+        Xr, Yr, _ = mlp.features(y[t - 8:t + 1])    # rows m * R + r
+        Xr = Xr.reshape(ne, R, 8).transpose(1, 0, 2)
+        Yr = Yr.reshape(ne, R).T
+        assert rel(X[t - 8], Xr) < 1e-6
+        assert rel(Y[t - 8], Yr) < 1e-6
+
+
+def test_set_solver_switches_mid_march(case):
+    """Direct for 25 steps, then GMRES (previous-step guess) on the same handle: the march continues
+    and matches the oracle; switching back to direct continues as well."""
+    import torch
+    from paper_2312_06367_gb300 import Solver
+    s = Solver(case["V"], case["F"], dt=DT, nt=NT, R=3).assemble()
+    s.set_excitation(case["pw"])
+    out = torch.zeros((NT, 3, s.ne), dtype=torch.float64, device="cuda")
+    s.step(25, out[:25])
+    s.set_solver("gmres", "prev", 1e-13)
+    s.step(20, out[25:45])
+    st = s.gmres_stats()
+    s.set_solver("direct")
+    s.step(NT - 45, out[45:])
+    torch.cuda.synchronize()
+    assert st["steps"] == 20 and st["not_converged"] == 0
+    assert rel(out.cpu().numpy().transpose(0, 2, 1), case["j"]) < 1e-10

@@ -148,3 +148,26 @@ def test_block_gemv_matches_numpy(dtype, tol, nblk, n, R):
     torch.cuda.synchronize()
     got = out.double().cpu().numpy()
     assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
+
+
+def test_replan_changes_precision_and_batch(ico1):
+    """One FP64 assembly, three plans: FP64 R=3, FP32 R=1 (the second wave alone), FP64 R=3 again."""
+    import torch
+    from paper_2312_06367_gb300 import Solver
+    V, F, pw, ops, fm, j_ref = ico1
+    s = Solver(V, F, dt=0.4, nt=40, R=3).assemble()
+    out = torch.zeros((40, 3, s.ne), dtype=torch.float64, device="cuda")
+    s.march(pw, out)
+    torch.cuda.synchronize()
+    assert rel(out.cpu().numpy().transpose(0, 2, 1), j_ref) < 1e-10
+    s.replan("fp32", 1)
+    one = {k: v[1:2] for k, v in pw.items()}
+    o1 = torch.zeros((40, 1, s.ne), dtype=torch.float32, device="cuda")
+    s.march(one, o1)
+    torch.cuda.synchronize()
+    assert rel(o1.double().cpu().numpy().transpose(0, 2, 1), j_ref[:, :, 1:2]) < 1e-5
+    s.replan("fp64", 3)
+    out2 = torch.zeros_like(out)
+    s.march(pw, out2)
+    torch.cuda.synchronize()
+    assert torch.equal(out, out2)
