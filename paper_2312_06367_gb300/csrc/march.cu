@@ -63,31 +63,79 @@ template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float4; };
 
+// Row dot products of one warp: acc[r] = B . x_r.  FP64: plain FP64 accumulation.  FP32: the
+// products and their sums are carried error-free (each product's rounding error from an FMA, each
+// addition's from Knuth's TwoSum), so the result equals the exact dot product of the FP32 inputs to
+// about FP32 precision squared; the lanes are combined in FP64.  The MOT recurrence turns y into the
+// current through (y_n - y_{n-1}) / dtt (Eq. post_processing), which magnifies any per-step error of
+// y by about |y| / |y_n - y_{n-1}|; plain FP32 accumulation over rows of thousands of entries is
+// then far above the reduced-precision bar at small time steps.
+template <typename T, int RMAX>
+struct RowDot {
+    __device__ static void run(const T* __restrict__ B, int ncols, const T* __restrict__ x, int R, int ldx,
+                               double* acc) {
+        const int lane = threadIdx.x & 31;
+        T s[RMAX];
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) s[r] = 0;
+        for (int j = lane; j < ncols; j += 32) {
+            const T a = B[j];
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r)
+                if (r < R) s[r] += a * x[(int64_t)r * ldx + j];
+        }
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) {
+            double v = (double)s[r];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            acc[r] = v;
+        }
+    }
+};
+
+template <int RMAX>
+struct RowDot<float, RMAX> {
+    __device__ static void run(const float* __restrict__ B, int ncols, const float* __restrict__ x, int R, int ldx,
+                               double* acc) {
+        const int lane = threadIdx.x & 31;
+        float hi[RMAX], lo[RMAX];
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) hi[r] = lo[r] = 0.f;
+        for (int j = lane; j < ncols; j += 32) {
+            const float a = B[j];
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r)
+                if (r < R) {
+                    const float xv = x[(int64_t)r * ldx + j];
+                    const float p = a * xv;
+                    const float pe = fmaf(a, xv, -p);          // a xv = p + pe exactly
+                    const float t = hi[r] + p;                  // TwoSum(hi, p) = t + te
+                    const float bp = t - hi[r];
+                    const float te = (hi[r] - (t - bp)) + (p - bp);
+                    hi[r] = t;
+                    lo[r] += te + pe;
+                }
+        }
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) {
+            double v = (double)hi[r] + (double)lo[r];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            acc[r] = v;
+        }
+    }
+};
+
 template <typename T, int RMAX>
 __device__ __forceinline__ void warp_rows(const T* __restrict__ B, int ncols, const T* __restrict__ x, int R,
                                           int ldx, double* acc) {
-    const int lane = threadIdx.x & 31;
-    T s[RMAX];
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) s[r] = 0;
-    for (int j = lane; j < ncols; j += 32) {
-        const T a = B[j];
-#pragma unroll
-        for (int r = 0; r < RMAX; ++r)
-            if (r < R) s[r] += a * x[(int64_t)r * ldx + j];
-    }
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-        T v = s[r];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc[r] = (double)v;
-    }
+    RowDot<T, RMAX>::run(B, ncols, x, R, ldx, acc);
 }
 
+// Per-block partial sums of the history, kept in FP64 for every path precision
 template <typename T, int RMAX>
 __global__ void k_history(const T* __restrict__ blocks, int nblk, int ne, int R, int ring, const Ctl* ctl,
                           const T* __restrict__ E, const T* __restrict__ H, const T* __restrict__ ringbuf,
-                          T* __restrict__ partial) {
+                          double* __restrict__ partial) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int q = blockIdx.y;
     if (warp >= ne) return;
@@ -104,16 +152,16 @@ __global__ void k_history(const T* __restrict__ blocks, int nblk, int ne, int R,
     double acc[RMAX];
     warp_rows<T, RMAX>(blocks + ((int64_t)q * ne + warp) * ne, ne, x, R, ne, acc);
     if ((threadIdx.x & 31) == 0)
-        for (int r = 0; r < R; ++r) partial[((int64_t)q * R + r) * ne + warp] = (T)acc[r];
+        for (int r = 0; r < R; ++r) partial[((int64_t)q * R + r) * ne + warp] = acc[r];
 }
 
 template <typename T>
-__global__ void k_reduce(const T* __restrict__ partial, int nblk, int ne, int R, T* __restrict__ b) {
+__global__ void k_reduce(const double* __restrict__ partial, int nblk, int ne, int R, T* __restrict__ b) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne * R) return;
-    T s = 0;
+    double s = 0;
     for (int q = 0; q < nblk; ++q) s += partial[(int64_t)q * R * ne + i];
-    b[i] = s;
+    b[i] = (T)s;
 }
 
 // y = M x for one square matrix, one warp per row; result to a ring slot or plain buffer
@@ -186,11 +234,11 @@ static cudaError_t launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
     const int wpb = 8;   // warps per block
     dim3 g((ne + wpb - 1) / wpb, p.nblk);
 #define HIST(RM) k_history<T, RM><<<g, 32 * wpb, 0, s>>>((const T*)p.blocks, p.nblk, ne, R, p.ring, p.ctl, \
-                                                           (const T*)p.E, (const T*)p.Hv, (const T*)p.ringbuf, (T*)p.partial)
+                                                           (const T*)p.E, (const T*)p.Hv, (const T*)p.ringbuf, (double*)p.partial)
 #define APPLY(RM, M, nr, nc_, x, y, rg) k_apply<T, RM><<<((nr) + wpb - 1) / wpb, 32 * wpb, 0, s>>>((const T*)(M), nr, nc_, R, (const T*)(x), (T*)(y), rg, p.ctl)
     cudaEventRecordWithFlags(p.evA, s, cudaEventRecordExternal);
     if (R == 1) HIST(1); else if (R <= 4) HIST(4); else HIST(8);
-    k_reduce<T><<<(ne * R + tb - 1) / tb, tb, 0, s>>>((const T*)p.partial, p.nblk, ne, R, (T*)p.b);
+    k_reduce<T><<<(ne * R + tb - 1) / tb, tb, 0, s>>>((const double*)p.partial, p.nblk, ne, R, (T*)p.b);
     cudaEventRecordWithFlags(p.evB, s, cudaEventRecordExternal);
     p.launches_per_step = 0;
     if (p.mlp_on) launch_mlp_guess<T>(&p, s);
@@ -366,7 +414,7 @@ tdcfie_status build_plan(tdcfie_t h) {
     CK(cudaMalloc(&p->Hv, es * R * ne));
     CK(cudaMalloc(&p->ringbuf, es * p->ring * R * ne));
     CK(cudaMalloc(&p->b, es * R * ne));
-    CK(cudaMalloc(&p->partial, es * p->nblk * R * ne));
+    CK(cudaMalloc(&p->partial, sizeof(double) * p->nblk * R * ne));
     CK(cudaMalloc(&p->z, es * R * nc));
     CK(cudaMalloc(&p->u, es * R * nc));
     if (tensor) {
