@@ -310,6 +310,55 @@ def run_guess_study(args, w):
     return 0
 
 
+def run_accuracy(args, w):
+    """Full-size accuracy of the reduced-precision paths: the workload's mesh and waves marched in
+    FP64 (the path that matches the oracle to 1e-10 on every case the oracle can assemble) as the
+    reference for 8 waves, then the same FP64-formed blocks re-planned for FP32 (R = 8) and for the
+    tensor-core FP16X3 path (all R waves); rel-L2 of the currents over all steps, edges and the 8 waves."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2312_06367_gb300 import Solver
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    R = int(w["pw"]["k"].shape[0])
+    nt = args.steps
+    pw8 = {k: v[:8] for k, v in w["pw"].items()}
+    t0 = time.time()
+    s = Solver(w["V"], w["F"], dt=w["dt"], nt=nt, alpha=w["alpha"], precision="fp64", R=8).assemble()
+    t_asm = time.time() - t0
+
+    def march(prec, r, pw):
+        s.replan(prec, r)
+        out = torch.zeros((nt, r, s.ne), dtype=s.dtype, device="cuda")
+        s.march(pw, out)
+        torch.cuda.synchronize()
+        return out[:, :8].double().cpu().numpy(), 1e3 / s.timing()["step_ms"]
+
+    ref, r64 = march("fp64", 8, pw8)
+    res = {"fp64": {"steps_s": r64}}
+    runs = [("fp32", 8, pw8)]
+    if R == 64:
+        runs.append(("fp16x3", 64, w["pw"]))
+    for prec, r, pw in runs:
+        j, rate = march(prec, r, pw)
+        err = float(np.linalg.norm(j - ref) / np.linalg.norm(ref))
+        win = {}
+        for a, b in ((0, nt // 4), (nt // 4, nt // 2), (nt // 2, nt)):
+            win[f"steps_{a}_{b}"] = float(np.linalg.norm(j[a:b] - ref[a:b]) / max(np.linalg.norm(ref[a:b]), 1e-300))
+        res[prec] = {"rel_l2_vs_fp64": err, "by_window": win, "steps_s": rate, "R": r}
+    line = {"metric": "rel-L2 of the surface current vs the FP64 path", "workload": w["name"],
+            "edges": s.ne, "K": s.K, "dt": w["dt"], "steps": nt, "waves_compared": 8,
+            "assemble_fp64_s": round(t_asm, 1), "results": res}
+    print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
 def run_ours(args, w):
     import numpy as np
     import torch
@@ -447,12 +496,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, help="override the workload's path precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="full-size accuracy of the reduced-precision paths against the FP64 path")
     ap.add_argument("--train-epochs", type=int, default=4, help="learned-guess training passes (ellipsoid12288)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     w = workload(args.workload, args.precision)
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.accuracy:
+        return run_accuracy(args, w)
     if args.workload == "ellipsoid12288":
         return run_guess_study(args, w)
     return run_ours(args, w)

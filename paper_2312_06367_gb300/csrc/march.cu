@@ -93,32 +93,55 @@ struct RowDot {
     }
 };
 
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);        // a b = p + pe exactly
+    const float t = hi + p;                  // TwoSum(hi, p) = t + te
+    const float bp = t - hi;
+    const float te = (hi - (t - bp)) + (p - bp);
+    hi = t;
+    lo += te + pe;
+}
+
 template <int RMAX>
 struct RowDot<float, RMAX> {
     __device__ static void run(const float* __restrict__ B, int ncols, const float* __restrict__ x, int R, int ldx,
                                double* acc) {
         const int lane = threadIdx.x & 31;
-        float hi[RMAX], lo[RMAX];
+        // four independent compensated accumulators per right-hand side (one per float4 component)
+        float hi[RMAX][4], lo[RMAX][4];
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r) hi[r] = lo[r] = 0.f;
-        for (int j = lane; j < ncols; j += 32) {
-            const float a = B[j];
+        for (int r = 0; r < RMAX; ++r)
 #pragma unroll
-            for (int r = 0; r < RMAX; ++r)
-                if (r < R) {
-                    const float xv = x[(int64_t)r * ldx + j];
-                    const float p = a * xv;
-                    const float pe = fmaf(a, xv, -p);          // a xv = p + pe exactly
-                    const float t = hi[r] + p;                  // TwoSum(hi, p) = t + te
-                    const float bp = t - hi[r];
-                    const float te = (hi[r] - (t - bp)) + (p - bp);
-                    hi[r] = t;
-                    lo[r] += te + pe;
-                }
+            for (int c = 0; c < 4; ++c) hi[r][c] = lo[r][c] = 0.f;
+        const bool vec = ((ncols | ldx) & 3) == 0 && ((reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(x)) & 15) == 0;
+        if (vec) {
+            const float4* B4 = reinterpret_cast<const float4*>(B);
+            for (int j = lane; j < (ncols >> 2); j += 32) {
+                const float4 a = B4[j];
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+                    if (r < R) {
+                        const float4 v = reinterpret_cast<const float4*>(x + (int64_t)r * ldx)[j];
+                        ff_add(hi[r][0], lo[r][0], a.x, v.x);
+                        ff_add(hi[r][1], lo[r][1], a.y, v.y);
+                        ff_add(hi[r][2], lo[r][2], a.z, v.z);
+                        ff_add(hi[r][3], lo[r][3], a.w, v.w);
+                    }
+            }
+        } else {
+            for (int j = lane; j < ncols; j += 32) {
+                const float a = B[j];
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+                    if (r < R) ff_add(hi[r][0], lo[r][0], a, x[(int64_t)r * ldx + j]);
+            }
         }
 #pragma unroll
         for (int r = 0; r < RMAX; ++r) {
-            double v = (double)hi[r] + (double)lo[r];
+            double v = 0.0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v += (double)hi[r][c] + (double)lo[r][c];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             acc[r] = v;
         }
@@ -151,8 +174,83 @@ __global__ void k_history(const T* __restrict__ blocks, int nblk, int ne, int R,
     }
     double acc[RMAX];
     warp_rows<T, RMAX>(blocks + ((int64_t)q * ne + warp) * ne, ne, x, R, ne, acc);
-    if ((threadIdx.x & 31) == 0)
-        for (int r = 0; r < R; ++r) partial[((int64_t)q * R + r) * ne + warp] = acc[r];
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+            if (r < R) partial[((int64_t)q * R + r) * ne + warp] = acc[r];
+    }
+}
+
+// FP32 history for several right-hand sides: one warp per ROWS rows, so that each lane's loads of
+// the R history vectors serve ROWS rows; error-free accumulation as in RowDot<float>
+template <int RMAX, int ROWS>
+__global__ void __launch_bounds__(256) k_history_rows(const float* __restrict__ blocks, int ne, int R, int ring,
+                                                      const Ctl* ctl, const float* __restrict__ E,
+                                                      const float* __restrict__ H, const float* __restrict__ ringbuf,
+                                                      double* __restrict__ partial) {
+    const int row0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * ROWS;
+    const int q = blockIdx.y;
+    if (row0 >= ne) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t n = ctl->n;
+    const float* x;
+    if (q == 0) x = E;
+    else if (q == 1) x = H;
+    else {
+        int64_t slot = (n - (q - 1)) % ring;
+        if (slot < 0) slot += ring;
+        x = ringbuf + slot * (int64_t)R * ne;
+    }
+    const float* Bq = blocks + (int64_t)q * ne * ne;
+    float hi[ROWS][RMAX], lo[ROWS][RMAX];
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i)
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) hi[i][r] = lo[i][r] = 0.f;
+    if ((ne & 3) == 0) {     // rows and vectors start on 16-byte boundaries
+        for (int j = lane; j < (ne >> 2); j += 32) {
+            float4 xv[RMAX];
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r)
+                if (r < R) xv[r] = reinterpret_cast<const float4*>(x + (int64_t)r * ne)[j];
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+                if (row0 + i >= ne) break;
+                const float4 a = reinterpret_cast<const float4*>(Bq + (int64_t)(row0 + i) * ne)[j];
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+                    if (r < R) {
+                        ff_add(hi[i][r], lo[i][r], a.x, xv[r].x);
+                        ff_add(hi[i][r], lo[i][r], a.y, xv[r].y);
+                        ff_add(hi[i][r], lo[i][r], a.z, xv[r].z);
+                        ff_add(hi[i][r], lo[i][r], a.w, xv[r].w);
+                    }
+            }
+        }
+    } else {
+        for (int j = lane; j < ne; j += 32) {
+            float xv[RMAX];
+#pragma unroll
+            for (int r = 0; r < RMAX; ++r)
+                if (r < R) xv[r] = x[(int64_t)r * ne + j];
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i) {
+                if (row0 + i >= ne) break;
+                const float a = Bq[(int64_t)(row0 + i) * ne + j];
+#pragma unroll
+                for (int r = 0; r < RMAX; ++r)
+                    if (r < R) ff_add(hi[i][r], lo[i][r], a, xv[r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < ROWS; ++i)
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) {
+            double v = (double)hi[i][r] + (double)lo[i][r];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && r < R && row0 + i < ne) partial[((int64_t)q * R + r) * ne + row0 + i] = v;
+        }
 }
 
 template <typename T>
@@ -174,8 +272,11 @@ __global__ void k_apply(const T* __restrict__ Mtx, int nrow, int ncol, int R, co
     warp_rows<T, RMAX>(Mtx + (int64_t)warp * ncol, ncol, x, R, ncol, acc);
     T* dst = y;
     if (ring > 0) dst = y + (ctl->n % ring) * (int64_t)R * nrow;
-    if ((threadIdx.x & 31) == 0)
-        for (int r = 0; r < R; ++r) dst[(int64_t)r * nrow + warp] = (T)acc[r];
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r)
+            if (r < R) dst[(int64_t)r * nrow + warp] = (T)acc[r];
+    }
 }
 
 // z[r][c] = sum_j tsign[c][j] w[r][tedge[c][j]],  w = (1/dtt - 1) y_n - y_{n-1}/dtt
@@ -237,7 +338,16 @@ static cudaError_t launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
                                                            (const T*)p.E, (const T*)p.Hv, (const T*)p.ringbuf, (double*)p.partial)
 #define APPLY(RM, M, nr, nc_, x, y, rg) k_apply<T, RM><<<((nr) + wpb - 1) / wpb, 32 * wpb, 0, s>>>((const T*)(M), nr, nc_, R, (const T*)(x), (T*)(y), rg, p.ctl)
     cudaEventRecordWithFlags(p.evA, s, cudaEventRecordExternal);
-    if (R == 1) HIST(1); else if (R <= 4) HIST(4); else HIST(8);
+    if (R == 1 || sizeof(T) == 8) {
+        if (R == 1) HIST(1); else if (R <= 4) HIST(4); else HIST(8);
+    } else {
+        // FP32 with several waves: 4 rows per warp up to 4 waves, 2 rows (fewer registers) above
+#define HISTR(RM, ROWS) k_history_rows<RM, ROWS><<<dim3((ne + wpb * ROWS - 1) / (wpb * ROWS), p.nblk), 32 * wpb, 0, s>>>( \
+            (const float*)p.blocks, ne, R, p.ring, p.ctl, (const float*)p.E, (const float*)p.Hv,                       \
+            (const float*)p.ringbuf, (double*)p.partial)
+        if (R <= 4) HISTR(4, 4); else HISTR(8, 2);
+#undef HISTR
+    }
     k_reduce<T><<<(ne * R + tb - 1) / tb, tb, 0, s>>>((const double*)p.partial, p.nblk, ne, R, (T*)p.b);
     cudaEventRecordWithFlags(p.evB, s, cudaEventRecordExternal);
     p.launches_per_step = 0;
