@@ -472,6 +472,16 @@ def run_ours(args, w):
     }
     if batched:
         line["batched_vs_plain"] = batched
+    acc = os.path.join(ROOT, "profiles", f"accuracy_{w['name']}.json")
+    if os.path.exists(acc):
+        try:
+            a = json.load(open(acc))["results"].get(prec)
+            if a:
+                line["accuracy"] = {"rel_l2_vs_fp64_path": a["rel_l2_vs_fp64"], "steps": json.load(open(acc))["steps"],
+                                    "waves": 8, "bar": 1e-5, "meets_bar": a["rel_l2_vs_fp64"] <= 1e-5,
+                                    "source": f"profiles/accuracy_{w['name']}.json (bench.py --accuracy)"}
+        except Exception:
+            pass
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n, t_casm = cpu_oracle_rate(w, 4 * args.steps + 50)
         sample = (f"{n} march steps of the same workload (assembly {t_casm:.1f} s untimed)" if t_casm is not None else
