@@ -35,7 +35,8 @@ typedef enum {
 } tdcfie_status;
 
 /* Arithmetic of the per-step history sum and solve (Sec. IV-B).  FP64: everything FP64.
- * FP32: FP32 matrices and vectors, FP32 accumulation (CUDA cores).  BF16X3: matrices and vectors
+ * FP32: FP32 matrices and vectors on CUDA cores; every row dot product is accumulated error-free
+ * (FMA product errors and TwoSum) and combined in FP64.  BF16X3: matrices and vectors
  * split into bf16 hi + lo, three tensor-core products (hi*hi + hi*lo + lo*hi) with FP32
  * accumulation.  FP16X3: the same with fp16 halves of power-of-two scaled values (per-row scales
  * of every matrix block, one scale per vector slot and right-hand side), about 2^-22 instead of
@@ -178,6 +179,27 @@ tdcfie_status tdcfie_replan(tdcfie_t h, int precision, int64_t max_rhs);
  * guess and GMRES tolerance as in tdcfie_opts.  The march state is kept; the step graph is captured
  * again at the next step.  GMRES statistics keep accumulating until the next set_excitation. */
 tdcfie_status tdcfie_set_solver(tdcfie_t h, int solver, int guess, double gmres_tol);
+
+/*
+ * Several scatterers marched together (the uneven-batch case; the paper marches one scatterer).
+ * A batch captures, at its first step, one CUDA graph that holds one step of every handle, each
+ * on its own stream branch; every tdcfie_batch_step then launches that graph once per step, so all
+ * handles advance together and their kernels run concurrently.  Each handle keeps its blocks, ring
+ * and step counter, and computes exactly what tdcfie_step computes.
+ *
+ * tdcfie_batch_create: handles (host array of n assembled handles on one device, each at most once)
+ * are borrowed, not owned: destroy the batch before any of them, and re-create it after
+ * tdcfie_replan or tdcfie_set_solver on a member.  Host work only, plus stream/event creation.
+ * tdcfie_batch_step: every handle must have its excitation set; currents_out is NULL (discard) or a
+ * host array of n DEVICE pointers laid out as in tdcfie_step for each handle (entries may be NULL).
+ * Synchronous; a member's non-finite current or device timeout is returned with its index.
+ * tdcfie_batch_timing: device time per batch step of the last call and kernel launches per step.
+ */
+typedef struct tdcfie_batch_s* tdcfie_batch_t;
+tdcfie_status tdcfie_batch_create(const tdcfie_t* handles, int64_t n, tdcfie_batch_t* out);
+tdcfie_status tdcfie_batch_step(tdcfie_batch_t b, int64_t nsteps, void* const* currents_out);
+tdcfie_status tdcfie_batch_timing(tdcfie_batch_t b, double* step_ms, int64_t* launches_per_step);
+tdcfie_status tdcfie_batch_destroy(tdcfie_batch_t b);
 
 /* Whole march: set_excitation, then nt steps into currents_out.  out_on_host != 0: currents_out is a
  * HOST buffer (pinned or pageable) and the device-to-host copy is part of the call. */

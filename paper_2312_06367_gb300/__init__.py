@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import BF16X3, FP16X3, FP32, FP64, TdcfieError  # noqa: F401
 
-__all__ = ["Solver", "block_gemv", "block_gemv_noalloc", "mlp_grad", "mlp_train", "mlp_predict", "mlp_samples",
+__all__ = ["Solver", "Batch", "block_gemv", "block_gemv_noalloc", "mlp_grad", "mlp_train", "mlp_predict", "mlp_samples",
            "FP64", "FP32", "BF16X3", "FP16X3", "TdcfieError"]
 
 
@@ -253,3 +253,33 @@ class Solver:
     def dtype(self):
         import torch
         return torch.float64 if self.precision == FP64 else torch.float32
+
+
+class Batch:
+    """Several assembled Solvers stepped by one graph launch per step (tdcfie_batch_*).
+
+    The solvers are borrowed: keep them alive and close the batch first."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s._h.value for s in self.solvers])
+        b = ctypes.c_void_p()
+        _lib.check(_lib.load().tdcfie_batch_create(arr, len(self.solvers), ctypes.byref(b)))
+        self._b = b
+
+    def step(self, nsteps: int, outs=None):
+        """outs: None, or one torch CUDA tensor (nsteps, R, ne) of the path dtype (or None) per solver."""
+        ptrs = None
+        if outs is not None:
+            ptrs = (ctypes.c_void_p * len(outs))(*[None if o is None else o.data_ptr() for o in outs])
+        _lib.check(_lib.load().tdcfie_batch_step(self._b, int(nsteps), ptrs))
+
+    def timing(self):
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _lib.check(_lib.load().tdcfie_batch_timing(self._b, ctypes.byref(ms), ctypes.byref(n)))
+        return {"step_ms": ms.value, "launches": n.value}
+
+    def close(self):
+        if getattr(self, "_b", None):
+            _lib.load().tdcfie_batch_destroy(self._b)
+            self._b = None

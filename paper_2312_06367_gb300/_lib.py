@@ -65,6 +65,10 @@ SIGNATURES = [
     ("tdcfie_mlp_load", _I, [_P, _P]),
     ("tdcfie_set_solver", _I, [_P, _I, _I, _D]),
     ("tdcfie_replan", _I, [_P, _I, _I64]),
+    ("tdcfie_batch_create", _I, [_P, _I64, _P]),
+    ("tdcfie_batch_step", _I, [_P, _I64, _P]),
+    ("tdcfie_batch_timing", _I, [_P, _P, _P]),
+    ("tdcfie_batch_destroy", _I, [_P]),
     ("tdcfie_destroy", _I, [_P]),
     ("tdcfie_last_error", ctypes.c_char_p, [_P]),
 ]

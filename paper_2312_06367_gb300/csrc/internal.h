@@ -135,4 +135,8 @@ tdcfie_status plan_reset(tdcfie_t h);
 tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout = nullptr);
 tdcfie_status plan_gmres_stats(tdcfie_t h, long long* out6);
 tdcfie_status plan_set_solver(tdcfie_t h, int solver, int guess, double tol);
+cudaError_t capture_step(tdcfie_t h, cudaStream_t s);
+tdcfie_status plan_set_outputs(tdcfie_t h, void* out, void* yout);
+tdcfie_status plan_check(tdcfie_t h);
+int plan_launches_per_step(tdcfie_t h);
 }  // namespace tdc

@@ -613,6 +613,44 @@ tdcfie_status plan_reset(tdcfie_t h) {
     return TDCFIE_OK;
 }
 
+// Enqueue one step of h on s (s must be capturing a graph).
+cudaError_t capture_step(tdcfie_t h, cudaStream_t s) {
+    StepPlan* p = h->plan;
+    if (p->prec == TDCFIE_FP64) return launch_step<double>(h, *p, s);
+    if (p->prec == TDCFIE_FP32) return launch_step<float>(h, *p, s);
+    launch_step_bf16x3(h, p, s);
+    return cudaGetLastError();
+}
+
+// Output base of the next steps of h (synchronous on h's stream): step n writes row n - n0.
+tdcfie_status plan_set_outputs(tdcfie_t h, void* out, void* yout) {
+    StepPlan* p = h->plan;
+    cudaStream_t s = h->stream;
+    Ctl c;
+    CK(cudaMemcpyAsync(&c, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c.n0 = c.n;
+    c.out = out;
+    c.yout = yout;
+    CK(cudaMemcpyAsync(p->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return TDCFIE_OK;
+}
+
+// Status words of the last steps of h (call after they completed)
+tdcfie_status plan_check(tdcfie_t h) {
+    StepPlan* p = h->plan;
+    Ctl c;
+    CK(cudaMemcpy(&c, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    if (c.timeout)
+        return fail(h, TDCFIE_E_TIMEOUT, "a bounded device-side wait ran out (tensor-core pipeline)");
+    if (c.status != 0)
+        return fail(h, TDCFIE_E_NONFINITE, "non-finite current at step " + std::to_string(c.bad_step));
+    return TDCFIE_OK;
+}
+
+int plan_launches_per_step(tdcfie_t h) { return h->plan ? h->plan->launches_per_step : 0; }
+
 tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout) {
     StepPlan* p = h->plan;
     cudaStream_t s = h->stream;

@@ -17,6 +17,7 @@ coupling alpha and the plane-wave batch.  Names state what they are:
                      dt 0.1, 1500 steps, GMRES tol 1e-8 (learned initial guess).
   sphere7680_train8  icosphere level 4, dt 0.1, 300 steps, 8 Fibonacci directions (seed 2312063671),
                      sigma 2: trajectories that train the learned GMRES guess.
+  batch_uneven       the first 16 scatterers of the batch32 family with at most 3456 edges.
   batch32            32 seeded scatterers (spheres, ellipsoids, tori) of 480..12288 edges, dt 0.2,
                      1000 steps, one direction each.
 """
@@ -68,11 +69,12 @@ def sphere7680_train8():
                 pw=excitation.fibonacci_batch(8, seed=2312063671, t0=8.0, sigma=2.0), precision="fp32")
 
 
-def batch32(seed: int = 2312063675, n: int = 32):
-    """32 seeded scatterers from size menus (edges 480..12288)."""
+def _family(seed: int):
+    """Endless seeded sequence of scatterers: sphere, ellipsoid (semi-axes U[0.5, 2]) or torus
+    (R 1, r U[0.2, 0.5]) from size menus of 480..12288 edges; one random plane wave each."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    probs = []
-    for s in range(n):
+    s = 0
+    while True:
         fam = int(rng.integers(0, 3))
         if fam == 0:
             lvl = int(rng.integers(2, 5))              # icosphere 480 / 1920 / 7680 edges
@@ -87,9 +89,25 @@ def batch32(seed: int = 2312063675, n: int = 32):
             rr = float(rng.uniform(0.2, 0.5))
             V, F = meshes.torus(1.0, rr, nu, nv)
         pw = excitation.random_batch(1, seed=seed + 1000 + s, t0=8.0, sigma=2.0)
-        probs.append(dict(name=f"batch32_{s}", V=V, F=F, dt=0.2, Nt=1000, alpha=1.0, pw=pw,
-                          precision="fp32"))
-    return probs
+        yield dict(name=f"batch32_{s}", V=V, F=F, dt=0.2, Nt=1000, alpha=1.0, pw=pw, precision="fp32")
+        s += 1
+
+
+def batch32(seed: int = 2312063675, n: int = 32):
+    """32 seeded scatterers from size menus (edges 480..12288)."""
+    g = _family(seed)
+    return [next(g) for _ in range(n)]
+
+
+def batch_uneven(n: int = 16, max_edges: int = 3456, seed: int = 2312063675):
+    """The first n scatterers of the same seeded family with at most max_edges edges (uneven sizes
+    whose assembly fits a short run)."""
+    out = []
+    for p in _family(seed):
+        if p["F"].shape[0] * 3 // 2 <= max_edges:
+            out.append(p)
+        if len(out) == n:
+            return out
 
 
 def small_sphere(level: int = 1, dt: float = 0.4, Nt: int = 40):
