@@ -108,6 +108,19 @@ def dist_env():
     return ws, rank, local
 
 
+def whole_job_rate(dev_ms: float, steps: int, ws: int, pg=None, device="cpu"):
+    """Whole-job steps/s of N replicas: every rank marched `steps` steps of its own batch in
+    dev_ms; the job takes the slowest rank's time (all-reduce MAX), and the value counts the steps
+    of all ranks.  Returns (value, max_ms)."""
+    import torch
+    tot_ms = float(dev_ms)
+    if pg is not None:
+        t = torch.tensor([float(dev_ms)], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    return ws * steps / (tot_ms / 1e3), tot_ms
+
+
 def cpu_oracle_dense_rate(w, steps: int = 3):
     """Oracle dense march (oracle.mot.march_dense, FP64 numpy) on blocks of the workload's size.
 
@@ -480,13 +493,7 @@ def run_ours(args, w):
     dev_ms = sum(step_ms)
     launches = s.timing()["launches"] if not flush else s.timing()["launches"] * args.steps
     finite = bool(torch.isfinite(out).all().item())
-    # max over ranks
-    tot_ms = dev_ms
-    if pg:
-        t = torch.tensor([dev_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = ws * args.steps / (tot_ms / 1e3)
+    value, tot_ms = whole_job_rate(dev_ms, args.steps, ws, pg, dev)
     # end-to-end through the C ABI with host buffers: excitation from host, currents to pinned host
     host_out = torch.empty((args.steps, R, s.ne), dtype=s.dtype, pin_memory=True).numpy()
     barrier()
