@@ -16,10 +16,13 @@
 //            (R x 64) with L2 evict-last, into a STAGES-deep ring of shared-memory stages;
 //   warp 1   one elected thread issues tcgen05.mma (M = 128, N = R, K = 16) and commits each
 //            stage back to the producer and each finished accumulator to the epilogue;
-//   warps 2-5 epilogue: after every block q, tcgen05.ld of the 128 x R FP32 accumulator (two
-//            TMEM buffers, so the MMAs of the next block overlap), scaling by the block's row
-//            and slot scales, FP32 accumulation in registers, and at a row-tile boundary a
-//            coalesced store of the partial sum.
+//   warps 2-5 epilogue: after every chunk (at most CHUNK_KT k tiles of one block q), tcgen05.ld
+//            of the 128 x R FP32 accumulator (two TMEM buffers, so the next chunk's MMAs
+//            overlap), scaling by the block's row and slot scales, error-free accumulation in
+//            registers (hi + lo pairs, TwoSum), and at a row-tile boundary a coalesced store of
+//            the partial sum.  The MOT post-processing differences consecutive y, which magnifies
+//            per-step errors of y about |y| / |y_n - y_{n-1}| times, so a long FP32 chain in
+//            tensor memory would dominate the error at small time steps.
 // Work split: stream-K over (row tile, q, k tile) iterations in row-tile-major order; a CTA's
 // contiguous range covers parts of at most a few row tiles ("segments").  A second kernel sums
 // the segment partials of every row tile in a fixed order (deterministic) and applies the
@@ -190,6 +193,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Accumulator chunks: the MMA warp and the epilogue walk the same sequence of chunks, each at most
+// CHUNK_KT k tiles of one (row tile, block q); a chunk never spans two blocks, so the block's row
+// and slot scales apply to the whole chunk.  Short chunks keep the FP32 accumulation chain in
+// tensor memory short; the epilogue sums the chunks error-free (hi + lo pairs and TwoSum).
+constexpr int CHUNK_KT = 2;
+
+__device__ __forceinline__ int64_t chunk_end(int64_t it, int64_t end, int ktiles) {
+    const int64_t kt = it % ktiles;
+    const int64_t qend = it - kt + ktiles;
+    const int64_t cend = it - kt + (kt / CHUNK_KT + 1) * CHUNK_KT;
+    const int64_t e = cend < qend ? cend : qend;
+    return e < end ? e : end;
+}
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+    const float t = hi + v;
+    const float bp = t - hi;
+    lo += (hi - (t - bp)) + (v - bp);
+    hi = t;
+}
+
 // ---------------------------------------------------------------- the GEMM kernel
 template <int N>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -255,9 +279,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             uint32_t ephase[2] = {0u, 0u};
             int chunk = 0;
             bool ok = true;
-            // one accumulator per (row tile, block q) chunk of the CTA's iteration range
+            // one accumulator per chunk (at most CHUNK_KT k tiles of one row tile and block q)
             for (int64_t it = begin; it < end && ok; ++chunk) {
-                const int64_t cend = (it / g.ktiles + 1) * g.ktiles < end ? (it / g.ktiles + 1) * g.ktiles : end;
+                const int64_t cend = chunk_end(it, end, g.ktiles);
                 const int buf = chunk & 1;
                 if (!mbar_wait(acc_empty + buf, ephase[buf] ^ 1u, ctl)) { ok = false; break; }
                 ephase[buf] ^= 1u;
@@ -290,12 +314,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
         uint32_t fphase[2] = {0u, 0u};
-        float accum[N];
+        float acc_hi[N], acc_lo[N];
 #pragma unroll
-        for (int c = 0; c < N; ++c) accum[c] = 0.f;
+        for (int c = 0; c < N; ++c) acc_hi[c] = acc_lo[c] = 0.f;
         int chunk = 0, seg = 0;
         for (int64_t it = begin; it < end; ++chunk) {
-            const int64_t cend = (it / g.ktiles + 1) * g.ktiles < end ? (it / g.ktiles + 1) * g.ktiles : end;
+            const int64_t cend = chunk_end(it, end, g.ktiles);
             const int64_t rt = it / ipt;
             const int q = (int)((it - rt * ipt) / g.ktiles);
             const int buf = chunk & 1;
@@ -311,8 +335,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * N + c0), v);
                 tmem_wait_ld();
 #pragma unroll
-                for (int c = 0; c < 32; ++c)
-                    accum[c0 + c] += __uint_as_float(v[c]) * sa * (sx ? sx[c0 + c] : 1.f);
+                for (int c = 0; c < 32; ++c)   // power-of-two scales: the products are exact
+                    two_sum_acc(acc_hi[c0 + c], acc_lo[c0 + c], __uint_as_float(v[c]) * sa * (sx ? sx[c0 + c] : 1.f));
             }
             tc_fence_before();
             mbar_arrive(acc_empty + buf);
@@ -321,8 +345,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 float* dst = g.partial + ((int64_t)blockIdx.x * g.maxseg + seg) * (int64_t)N * BM;
 #pragma unroll
                 for (int c = 0; c < N; ++c) {
-                    dst[(int64_t)c * BM + row] = accum[c];
-                    accum[c] = 0.f;
+                    dst[(int64_t)c * BM + row] = acc_hi[c] + acc_lo[c];
+                    acc_hi[c] = acc_lo[c] = 0.f;
                 }
                 ++seg;
             }
