@@ -94,3 +94,35 @@ def test_t0_well_conditioned_across_dt():
     V, F = meshes.icosphere(1)
     conds = [np.linalg.cond(Formulation(Operators(V, F, dt=dt)).T(0)) for dt in (0.1, 1.0, 10.0, 100.0)]
     assert max(conds) < 10.0
+
+
+def test_t0_block_scaling_large_dt():
+    """Large-time-step balance of the combined operator (Sec. IV, the scaling table of Eq.
+    qHP_TDCFIE): in the [Lambda, Sigma] bases of the tested (rows: PP^Lambda, PP^{Sigma H}) and the
+    unknown (columns: P^{Lambda H}, P^Sigma) spaces of the sphere (no harmonic part), the
+    (Lambda, Sigma) block of T_0 falls as dt^-1 and the two diagonal blocks stay O(1).  The remaining
+    (Sigma, Lambda) block vanishes in the continuous setting by the static MFIE property; discretely
+    it is dtt times the residual PP^{Sigma H} (G/2 - M) G^-1 (G/2 + MM_0) P^{Lambda H}, which is small
+    and whose dt-growth is exactly that factor."""
+    V, F = meshes.icosphere(1)
+    dts = (10.0, 100.0, 1000.0)
+    blocks = {}
+    resid = []
+    for dt in dts:
+        ops = Operators(V, F, dt=dt)
+        fm = Formulation(ops)
+        T0 = fm.T(0)
+        for rn, R in (("L", fm.PPL), ("S", fm.PPSH)):
+            for cn, C in (("L", fm.PLH), ("S", fm.PS)):
+                blocks.setdefault(rn + cn, []).append(np.linalg.norm(R @ T0 @ C))
+        MM0 = ops.MM[0]
+        res = fm.PPSH @ (0.5 * ops.G - ops.M) @ np.linalg.inv(ops.G) @ (0.5 * ops.G + MM0) @ fm.PLH
+        resid.append(np.linalg.norm(res))
+    slope = {k: np.polyfit(np.log(dts), np.log(v), 1)[0] for k, v in blocks.items()}
+    assert abs(slope["LS"] + 1.0) < 0.3
+    assert abs(slope["LL"]) < 0.3 and abs(slope["SS"]) < 0.3
+    # (Sigma, Lambda): small against the diagonal blocks over the range, and dtt-proportional
+    assert max(blocks["SL"]) < 0.05 * min(min(blocks["LL"]), min(blocks["SS"]))
+    ratio = np.array(blocks["SL"][1:]) / np.array(dts[1:])     # once MM_0 has reached its static limit
+    assert np.max(ratio) / np.min(ratio) < 1.1
+    assert max(resid) < 1e-2 * np.linalg.norm(0.5 * Operators(V, F, dt=dts[0]).G)
