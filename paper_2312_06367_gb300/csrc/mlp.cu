@@ -278,13 +278,10 @@ using namespace tdc;
 
 static tdcfie_status launch_grad(const float* params, const float* X, const float* Y, int64_t n, int64_t off,
                                  int64_t count, float* grad, float* loss, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             GRAD_SMEM * (int)sizeof(float));
-        if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaFuncSetAttribute (MLP gradient)");
-        attr = true;
-    }
+    // set on every call: the attribute is per device, and the call is cheap next to a training step
+    const cudaError_t ea = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                GRAD_SMEM * (int)sizeof(float));
+    if (ea != cudaSuccess) return cuda_fail(nullptr, ea, "cudaFuncSetAttribute (MLP gradient)");
     const unsigned blocks = (unsigned)((count + TS - 1) / TS);
     k_mlp_grad<<<blocks, 256, GRAD_SMEM * sizeof(float), s>>>(params, X, Y, n, off, count, 1.f / (float)count, grad,
                                                               loss);

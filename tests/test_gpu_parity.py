@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle, same seeded inputs.
 
-Tolerances (the stated spec bars): FP64 path rel-L2 <= 1e-10, reduced precision <= 1e-5
+Tolerances (the accuracy bars of the two path classes): FP64 path rel-L2 <= 1e-10, reduced precision <= 1e-5
 on the surface current j (all steps x edges x right-hand sides); assembled FP64 matrices per block
 within 1e-10 relative Frobenius (atomic summation order only).
 """
