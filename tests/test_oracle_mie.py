@@ -63,7 +63,8 @@ def test_mot_sphere_currents_match_mie_transient():
     fm = Formulation(ops)
     t = w["dt"] * np.arange(1, w["Nt"] + 1)
     e, h = rhs.incident_tests(ops, w["pw"], t)
-    j = fm.postprocess(mot.march_factored(fm, fm.rhs(e, h)))[:, :, 0]
+    y = mot.march_factored(fm, fm.rhs(e, h))
+    j = fm.postprocess(y)[:, :, 0]
     p = points()
     J_mot = current_at(ops.topo, j, p)
     J_mie = mie_current(p, t)
@@ -71,3 +72,8 @@ def test_mot_sphere_currents_match_mie_transient():
     err_obs = np.linalg.norm(J_mot[:, 0] - J_mie[:, 0]) / np.linalg.norm(J_mie[:, 0])
     print(f"MOT vs Mie transient: rel-L2 {err:.3f} (observation point {err_obs:.3f})")
     assert err < 0.15
+    # planted mistake: the post-processing with the loop/star projectors swapped must fail the pin
+    yp = np.concatenate([np.zeros_like(y[:1]), y[:-1]], axis=0)
+    bad = (np.einsum("ab,nbr->nar", fm.PS, y) + np.einsum("ab,nbr->nar", fm.PLH, y - yp) / fm.dtt)[:, :, 0]
+    err_bad = np.linalg.norm(current_at(ops.topo, bad, p) - J_mie) / np.linalg.norm(J_mie)
+    assert err_bad > 3 * 0.15
