@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import subprocess
 import sys
@@ -30,18 +31,30 @@ def _compile(src: str, extra: list[str]) -> str:
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj
     lang = ["-x", "cu"] if src.endswith(".cpp") else []
-    cmd = [_nvcc()] + ARCH + FLAGS + extra + lang + ["-c", path, "-o", obj]
+    tmp = obj + f".{os.getpid()}.tmp"
+    cmd = [_nvcc()] + ARCH + FLAGS + extra + lang + ["-c", path, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
     if r.stderr.strip():
         sys.stderr.write(r.stderr)
+    os.replace(tmp, obj)
     return obj
 
 
 def build(verbose: bool = False, extra: list[str] | None = None) -> str:
+    """Compile what is out of date and link.  Several processes (one per rank) may call this at
+    once: an exclusive lock serialises them, and objects and library are renamed into place."""
     os.makedirs(BUILD, exist_ok=True)
-    extra = extra or []
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(verbose, extra or [])
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool, extra: list[str]) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     if not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
