@@ -130,7 +130,8 @@ tdcfie_status tdcfie_gmres_stats(tdcfie_t h, int64_t* inner_iterations, int64_t*
 /*
  * Learned initial guess for the GMRES solve (an extension: the paper solves with T_0 directly).
  * For unknown m of right-hand side r at step n the features are x = (y_{n-1}, ..., y_{n-8})_{r,m} / s,
- * s = RMS over edges of y_{n-1} for that r (1 if zero), and the guess is s f(x) with the network
+ * s = RMS over edges of y_{n-1} for that r (1 if zero), and the guess is y_{n-1} + s f(x) (the network
+ * predicts the increment, so a zero network gives the previous-step guess) with
  *   f(x) = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3,  W1 64 x 8, W2 64 x 64, w3 64.
  * Parameters: 4801 float32 in the order W1 (row-major), b1, W2 (row-major), b2, w3, b3.
  * Samples: X n x 8 float32 features (row-major), Y n float32 targets.
@@ -157,7 +158,7 @@ tdcfie_status tdcfie_mlp_predict(const float* params, const float* X, int64_t n,
 /* Training samples from a stored march: y (DEVICE, nt x R x N_E, float64 for precision
  * TDCFIE_FP64 or float32 for TDCFIE_FP32, as written by tdcfie_step_y).  For t = 8 .. nt-1 (0-based
  * rows of y) and every r, m, sample s = ((t - 8) R + r) N_E + m gets X[s] = (y[t-1] .. y[t-8])_{r,m} / sc
- * and Y[s] = y[t]_{r,m} / sc, sc = RMS over edges of y[t-1]_r (1 if zero), FP32 arithmetic: the
+ * and Y[s] = (y[t] - y[t-1])_{r,m} / sc, sc = RMS over edges of y[t-1]_r (1 if zero), FP32 arithmetic: the
  * features the march evaluates before each GMRES solve.  X (DEVICE) holds (nt - 8) R N_E x 8 floats,
  * Y (nt - 8) R N_E.  Needs nt >= 9. */
 tdcfie_status tdcfie_mlp_samples(int precision, const void* y, int64_t nt, int64_t R, int64_t ne, float* X, float* Y,
@@ -165,7 +166,7 @@ tdcfie_status tdcfie_mlp_samples(int precision, const void* y, int64_t nt, int64
 
 /* Load network parameters (HOST, 4801 floats) into an assembled handle (K - 1 >= 8); they are used
  * while the solver is GMRES with guess TDCFIE_GUESS_MLP.  Synchronous.  Until loaded the weights are
- * zero and so is the guess. */
+ * zero, so the guess is the previous step. */
 tdcfie_status tdcfie_mlp_load(tdcfie_t h, const float* params);
 
 /* Rebuild the step plan of an assembled handle for another path precision and number of

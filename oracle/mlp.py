@@ -49,12 +49,14 @@ def loss_and_grad(theta, X, Y):
 
 
 def features(y_hist):
-    """y_hist: (9, ne, R) = y_{n-8} .. y_n.  Returns X (ne R, 8) = y_{n-1..n-8}/s_n and target y_n/s_n."""
+    """y_hist: (9, ne, R) = y_{n-8} .. y_n.  Returns X (ne R, 8) = y_{n-1..n-8}/s_n and the target
+    (y_n - y_{n-1})/s_n: the network predicts the increment, so a zero output is the previous-step
+    guess."""
     prev = y_hist[-2]                                   # y_{n-1}
     s = np.sqrt(np.mean(prev ** 2, axis=0))             # per right-hand side
     s = np.where(s > 0, s, 1.0)
     X = np.stack([y_hist[-2 - k] / s for k in range(8)], axis=-1)   # (ne, R, 8)
-    Y = y_hist[-1] / s
+    Y = (y_hist[-1] - y_hist[-2]) / s
     return X.reshape(-1, 8), Y.reshape(-1), s
 
 

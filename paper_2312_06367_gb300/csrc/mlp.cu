@@ -1,7 +1,8 @@
 // Learned initial guess for the per-step GMRES solve (no counterpart in the paper).
 //
 // Per unknown m at step n: features x = (y_{n-1} .. y_{n-8})_m / s_n with s_n = RMS_m (y_{n-1})_m,
-// network 8 -> 64 -> 64 -> 1 with tanh hidden layers, prediction y_{n,m} = s_n f(x).
+// network 8 -> 64 -> 64 -> 1 with tanh hidden layers, prediction y_{n,m} = y_{n-1,m} + s_n f(x) (the
+// network learns the increment; a zero output is the previous-step guess).
 // Parameters (FP32 master, 4801 floats): W1 (64 x 8), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3.
 // Training: mini-batch squared error (1/2N) sum (f(x) - t)^2, gradient by these kernels (64-sample
 // tiles in shared memory, per-block partial gradients added with atomics), Adam update.
@@ -195,11 +196,11 @@ __global__ void k_mlp_samples(const T* __restrict__ y, int R, int ne, float* __r
     for (int m = threadIdx.x; m < ne; m += blockDim.x) {
         const int64_t o = q * ne + m;
         for (int k = 1; k <= NIN; ++k) X[o * NIN + k - 1] = (float)at(t - k)[m] / s;
-        Y[o] = (float)at(t)[m] / s;
+        Y[o] = ((float)at(t)[m] - (float)at(t - 1)[m]) / s;
     }
 }
 
-// guess[r][m] = s_r f((y_{n-1..n-8})_{r,m} / s_r); y_i = 0 for i <= 0
+// guess[r][m] = y_{n-1} + s_r f((y_{n-1..n-8})_{r,m} / s_r); y_i = 0 for i <= 0
 template <typename T>
 __global__ void k_mlp_guess(const __half* __restrict__ wh, const T* __restrict__ ringbuf, int ring, int R, int ne,
                             const Ctl* ctl, const float* __restrict__ scale, T* __restrict__ guess) {
@@ -220,7 +221,7 @@ __global__ void k_mlp_guess(const __half* __restrict__ wh, const T* __restrict__
         }
         x[k - 1] = v / s;
     }
-    guess[(int64_t)r * ne + m] = (T)(s * mlp_forward(P, x));
+    guess[(int64_t)r * ne + m] = (T)(s * (x[0] + mlp_forward(P, x)));   // y_{n-1} + predicted increment
 }
 
 // ---------------------------------------------------------------- march integration

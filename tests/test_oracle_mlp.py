@@ -32,4 +32,4 @@ def test_features_definition():
     assert np.allclose(s, np.sqrt(np.mean(yh[7] ** 2, axis=0)))
     assert np.allclose(X.reshape(5, 2, 8)[3, 1, 0], yh[7, 3, 1] / s[1])
     assert np.allclose(X.reshape(5, 2, 8)[3, 1, 7], yh[0, 3, 1] / s[1])
-    assert np.allclose(Y.reshape(5, 2)[4, 0], yh[8, 4, 0] / s[0])
+    assert np.allclose(Y.reshape(5, 2)[4, 0], (yh[8, 4, 0] - yh[7, 4, 0]) / s[0])
