@@ -199,41 +199,18 @@ def run_reference(args, w):
     return 0
 
 
-def batched_vs_plain(s, w, host_out, batched_steps_s, stream, args):
-    """The plain GPU march of one incident wave (FP32 path, R = 1, same assembled blocks) against
-    the batched tensor-core march of all R waves: rates per wave-step and the currents of wave 0
-    over the same steps (rel-L2 of the two)."""
-    import numpy as np
-    import torch
-    R = int(w["pw"]["k"].shape[0])
-    nst = host_out.shape[0]
-    s.replan("fp32", 1)
-    one = {k: v[:1] for k, v in w["pw"].items()}
-    out1 = torch.empty((nst, 1, s.ne), dtype=torch.float32, device="cuda")
-    with torch.cuda.stream(stream):
-        s.march(one, out1)                       # warm-up pass (captures the step graph)
-        s.march(one, out1)
-        torch.cuda.synchronize()
-    plain = 1e3 / s.timing()["step_ms"]
-    a = out1[:, 0, :].double().cpu().numpy()
-    b = host_out[:, 0, :].astype(np.float64)
-    err = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-    return {"plain": "FP32 history sum, R = 1 (one incident wave per march), same blocks",
-            "plain_steps_s": plain, "plain_wave_steps_s": plain, "batched_wave_steps_s": batched_steps_s * R,
-            "speedup_per_wave": batched_steps_s * R / plain, "steps_compared": nst,
-            "rel_l2_wave0_batched_vs_plain": err}
-
-
 def run_guess_study(args, w):
-    """The learned GMRES initial guess: trained on 7680-edge sphere trajectories, evaluated on the
-    12288-edge ellipsoid against zero and previous-step guesses and the direct T_0^-1 solve (the
-    plain GPU march), all on one assembled handle at FP32 with GMRES tol 1e-8."""
+    """GMRES initial guesses on the 12288-edge ellipsoid (FP32, GMRES tol 1e-8), against the direct
+    T_0^-1 solve (the plain GPU march): zero, previous step, cubic extrapolation of the last four
+    steps, and two learned networks trained on 7680-edge sphere trajectories -- the increment over
+    y_{n-1} and the correction to the extrapolation.  Reported per guess: steps/s, GMRES iterations,
+    the guess error |x0 - y_n| / |y_n| over the march, rel-L2 against the direct march."""
     import numpy as np
     import torch
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2312_06367_gb300 import Solver, mlp_samples, mlp_train
+    from paper_2312_06367_gb300 import Solver, mlp_predict, mlp_samples, mlp_train
     from synth import workloads
     ws, rank, local = dist_env()
     if rank != 0:
@@ -241,7 +218,7 @@ def run_guess_study(args, w):
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     info = {}
-    # 1. training trajectories (plain FP32 direct march of 8 waves) and samples, on the GPU
+    # 1. training trajectories (plain FP32 direct march of 8 waves) on the GPU
     tw = workloads.sphere7680_train8()
     t0 = time.time()
     st = Solver(tw["V"], tw["F"], dt=tw["dt"], nt=tw["Nt"], precision="fp32", R=8, stream=stream.cuda_stream).assemble()
@@ -250,57 +227,83 @@ def run_guess_study(args, w):
     with torch.cuda.stream(stream):
         st.set_excitation(tw["pw"])
         st.step_y(tw["Nt"], None, y)
-        X, Y = mlp_samples(y)
         torch.cuda.synchronize()
     st.close()
+    # 2. one network per base (Adam, GPU kernels); seeded uniform(+-1/sqrt(fan_in)) weights, zero biases
+    nets = {}
+    for base in ("prev", "extrap"):
+        with torch.cuda.stream(stream):
+            X, Y = mlp_samples(y, base=base)
+        rng = np.random.default_rng(2312063672)
+        parts = []
+        for fan_in, n_w, n_b in ((8, 64 * 8, 64), (64, 64 * 64, 64), (64, 64, 1)):
+            lim = 1.0 / np.sqrt(fan_in)
+            parts += [rng.uniform(-lim, lim, n_w), np.zeros(n_b)]
+        params = torch.tensor(np.concatenate(parts), dtype=torch.float32, device="cuda")
+        t0 = time.time()
+        with torch.cuda.stream(stream):
+            hist = mlp_train(params, X, Y, epochs=args.train_epochs, batch=4096, lr=1e-3, seed=7)
+        torch.cuda.synchronize()
+        info[base] = dict(train_samples=int(X.shape[0]), train_epochs=args.train_epochs,
+                          train_s=round(time.time() - t0, 2), loss_first=float(hist[0]), loss_last=float(hist[-1]))
+        nets[base] = params
+        del X, Y
     del y
-    # 2. training (Adam, GPU kernels); initial parameters: uniform(+-1/sqrt(fan_in)), zero biases
-    rng = np.random.default_rng(2312063672)
-    parts = []
-    for fan_in, n_w, n_b in ((8, 64 * 8, 64), (64, 64 * 64, 64), (64, 64, 1)):
-        lim = 1.0 / np.sqrt(fan_in)
-        parts += [rng.uniform(-lim, lim, n_w), np.zeros(n_b)]
-    params = torch.tensor(np.concatenate(parts), dtype=torch.float32, device="cuda")
-    t0 = time.time()
-    with torch.cuda.stream(stream):
-        hist = mlp_train(params, X, Y, epochs=args.train_epochs, batch=4096, lr=1e-3, seed=7)
-    torch.cuda.synchronize()
-    info.update(train_samples=int(X.shape[0]), train_epochs=args.train_epochs, train_s=round(time.time() - t0, 2),
-                train_loss_first=float(hist[0]), train_loss_last=float(hist[-1]))
-    del X, Y
     torch.cuda.empty_cache()                      # the evaluation assembly needs most of the HBM
-    # 3. evaluation handle
+    # 3. evaluation handle; the direct march's y gives the guess errors
     t0 = time.time()
     s = Solver(w["V"], w["F"], dt=w["dt"], nt=w["Nt"], alpha=w["alpha"], precision="fp32", R=1,
                stream=stream.cuda_stream, solver="gmres", guess="zero", gmres_tol=w["gmres_tol"]).assemble()
     t_asm = time.time() - t0
-    s.mlp_load(params.cpu().numpy())
     nt = w["Nt"]
     outs, rows = {}, {}
-    for mode in ("direct", "zero", "prev", "mlp"):
+    yd = torch.empty((nt, 1, s.ne), dtype=torch.float32, device="cuda")
+    for mode in ("direct", "zero", "prev", "extrap", "mlp", "mlp_extrap"):
         if mode == "direct":
             s.set_solver("direct")
         else:
             s.set_solver("gmres", mode, w["gmres_tol"])
+            if mode.startswith("mlp"):
+                s.mlp_load(nets["extrap" if mode == "mlp_extrap" else "prev"].cpu().numpy())
         out = torch.empty((nt, 1, s.ne), dtype=torch.float32, device="cuda")
         with torch.cuda.stream(stream):
             s.set_excitation(w["pw"])
             s.step(args.warmup)                   # warm-up: captures the step graph
             torch.cuda.synchronize()
             with Clocks(local) as clk:
-                s.march(w["pw"], out)
+                s.set_excitation(w["pw"])
+                if mode == "direct":
+                    s.step_y(nt, out, yd)
+                else:
+                    s.step(nt, out)
                 torch.cuda.synchronize()
         tm = s.timing()
         row = {"steps_s": 1e3 / tm["step_ms"], "ms_per_step": tm["step_ms"], "history_ms": tm["history_ms"],
                "launches": tm["launches"], "clocks": clk.summary()}
         if mode != "direct":
             row.update(s.gmres_stats())
+            row["iterations_per_step"] = row["iterations"] / max(row["steps"], 1)
         rows[mode] = row
         outs[mode] = out[:, 0, :].double()
     ref = outs["direct"]
     for mode in rows:
         rows[mode]["rel_l2_vs_direct"] = float(torch.linalg.norm(outs[mode] - ref) / torch.linalg.norm(ref))
-    m = rows["mlp"]
+    # guess errors |x0 - y_n| / |y_n| over steps 9 .. nt of the direct march (analysis, on the device)
+    yv = yd[:, 0, :].double()
+    yn, y1, y2, y3, y4 = yv[8:], yv[7:-1], yv[6:-2], yv[5:-3], yv[4:-4]
+    ext = 4 * y1 - 6 * y2 + 4 * y3 - y4
+    sc = torch.sqrt(torch.mean(y1 ** 2, dim=1, keepdim=True))
+    sc = torch.where(sc > 0, sc, torch.ones_like(sc))
+    Xf, _ = mlp_samples(yd)
+    den = torch.linalg.norm(yn)
+    gerr = {"zero": 1.0, "prev": float(torch.linalg.norm(yn - y1) / den), "extrap": float(torch.linalg.norm(yn - ext) / den)}
+    for mode, base in (("mlp", y1), ("mlp_extrap", ext)):
+        f = mlp_predict(nets["extrap" if mode == "mlp_extrap" else "prev"], Xf).double().reshape(nt - 8, s.ne)
+        gerr[mode] = float(torch.linalg.norm(yn - (base + sc.float().double() * f)) / den)
+    for mode in gerr:
+        rows[mode]["guess_error"] = gerr[mode]
+    best = min(("zero", "prev", "extrap", "mlp", "mlp_extrap"), key=lambda m: rows[m]["ms_per_step"])
+    m = rows[best]
     pk = peaks()
     hb = s.timing()["history_bytes"]
     line = {
@@ -308,7 +311,7 @@ def run_guess_study(args, w):
         "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["name"], "edges": s.ne, "triangles": s.nc, "R": 1, "K": s.K, "dt": w["dt"],
-                   "solver": "gmres", "guess": "mlp", "gmres_tol": w["gmres_tol"], "assemble_s": round(t_asm, 1),
+                   "solver": "gmres", "guess": best, "gmres_tol": w["gmres_tol"], "assemble_s": round(t_asm, 1),
                    "cache": "inputs larger than L2"},
         "gpu_launches": int(m["launches"]),
         "roofline": {"bound": "hbm", "achieved": hb / (m["history_ms"] / 1e3) / 1e9 if m["history_ms"] else None,
@@ -372,9 +375,10 @@ def run_accuracy(args, w):
     return 0
 
 
-def run_batch(args, probs):
-    """Uneven batch: every scatterer marched by one graph launch per step (tdcfie_batch_step)
-    against the same handles stepped one after another (tdcfie_step each), FP32, one wave each."""
+def run_batch(args, probs, name):
+    """Uneven batch: every scatterer FP32 with one wave, all advanced by one graph launch per step
+    (tdcfie_batch_step: the persistent cooperative kernel, launch shape from tdcfie_batch_tune),
+    against the same handles stepped one after another (tdcfie_step each)."""
     import torch
 
     import __graft_entry__
@@ -386,9 +390,11 @@ def run_batch(args, probs):
     torch.cuda.set_device(local)
     t0 = time.time()
     ss = []
-    for p in probs:
+    for p in sorted(probs, key=lambda p: -p["F"].shape[0]):     # largest first: the FP64 peak is lowest
         s = Solver(p["V"], p["F"], dt=p["dt"], nt=args.steps, alpha=p["alpha"], precision="fp32", R=1).assemble()
+        s.release_assembly()                 # keep only the FP32 step plan on the device
         s.set_excitation(p["pw"])
+        s._p = p
         ss.append(s)
     t_asm = time.time() - t0
     # one after another: each handle's own graph, warmed up, then timed
@@ -397,9 +403,12 @@ def run_batch(args, probs):
         s.step(args.warmup)
         s.step(args.steps)
         seq_ms += s.timing()["step_ms"]
-    for s, p in zip(ss, probs):
-        s.set_excitation(p["pw"])
+    for s in ss:
+        s.set_excitation(s._p["pw"])
     b = Batch(ss)
+    t1 = time.time()
+    cfg = b.tune(3)
+    t_tune = time.time() - t1
     b.step(args.warmup)
     outs = [torch.empty((args.steps, 1, s.ne), dtype=torch.float32, device="cuda") for s in ss]
     with Clocks(local) as clk:
@@ -412,16 +421,16 @@ def run_batch(args, probs):
         "metric": METRIC, "value": 1e3 / t["step_ms"], "unit": "steps/s (all scatterers advance one step)",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t["step_ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batch_uneven{len(probs)}", "scatterers": len(probs),
-                   "edges": [s.ne for s in ss], "K": [s.K for s in ss], "dt": probs[0]["dt"],
-                   "assemble_s": round(t_asm, 1), "cache": "history operands of all scatterers "
-                   f"({hb / 1e9:.2f} GB) stream each step", "finite": finite},
+        "config": {"workload": name, "scatterers": len(ss), "edges": [s.ne for s in ss], "K": [s.K for s in ss],
+                   "dt": probs[0]["dt"], "assemble_s": round(t_asm, 1), "tune_s": round(t_tune, 2), "launch": cfg,
+                   "cache": f"history operands of all scatterers ({hb / 1e9:.2f} GB) stream each step",
+                   "finite": finite},
         "gpu_launches": int(t["launches"]) * args.steps,
         "sequential": {"ms_per_step": seq_ms, "steps_s": 1e3 / seq_ms, "how": "each handle's own step graph, one after another"},
         "speedup_vs_sequential": seq_ms / t["step_ms"],
         "roofline": {"bound": "hbm", "achieved": hb / (t["step_ms"] / 1e3) / 1e9, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                      "frac": hb / (t["step_ms"] / 1e3) / 1e9 / pk["hbm_gbs"], "traffic": None,
-                     "kernel": "whole batch step (history sums dominate)", "algorithmic_bytes_per_launch": hb},
+                     "kernel": "whole batch step (k_batch_step; history rows dominate)", "algorithmic_bytes_per_launch": hb},
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -429,6 +438,37 @@ def run_batch(args, probs):
     for s in ss:
         s.close()
     return 0
+
+
+def accuracy_in_run(s, w, nt, stream):
+    """Measured in this run on the same FP64-formed blocks: the FP64 path (the path that matches
+    the oracle to 1e-10 wherever the oracle can assemble) marches the first 8 waves for nt steps;
+    the timed path (all waves) and the plain single-wave FP32 path march the same steps; rel-L2 of
+    the currents over steps x edges x waves against the FP64 march."""
+    import numpy as np
+    import torch
+    R = int(w["pw"]["k"].shape[0])
+    prec = w["precision"]
+    pw8 = {k: v[:8] for k, v in w["pw"].items()}
+    pw1 = {k: v[:1] for k, v in w["pw"].items()}
+
+    def march(p, r, pw):
+        s.replan(p, r)
+        out = torch.zeros((nt, r, s.ne), dtype=s.dtype, device="cuda")
+        with torch.cuda.stream(stream):
+            s.march(pw, out)
+        torch.cuda.synchronize()
+        return out.double().cpu().numpy()
+
+    ref = march("fp64", min(8, R), pw8)
+    got = march(prec, R, w["pw"])[:, :ref.shape[1]]
+    one = march("fp32", 1, pw1)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    res = {"steps": nt, "waves": ref.shape[1], "reference": "FP64 path on the same FP64-formed blocks",
+           "rel_l2_vs_fp64_path": rel(got, ref), "plain_fp32_rel_l2_vs_fp64_path": rel(one, ref[:, :1]),
+           "bar": 1e-5}
+    res["meets_bar"] = res["rel_l2_vs_fp64_path"] <= 1e-5
+    return res
 
 
 def run_ours(args, w):
@@ -450,9 +490,13 @@ def run_ours(args, w):
     stream = torch.cuda.Stream(device=dev)
     R = int(w["pw"]["k"].shape[0])
     prec = w["precision"]
+    tensor = prec in ("bf16x3", "fp16x3")
     t0 = time.time()
-    s = Solver(w["V"], w["F"], dt=w["dt"], nt=args.steps, alpha=w["alpha"], precision=prec, R=R,
-               stream=stream.cuda_stream, device=local).assemble()
+    # the blocks are formed in FP64 so that the FP64 path can check the timed path in this run
+    s = Solver(w["V"], w["F"], dt=w["dt"], nt=args.steps, alpha=w["alpha"], precision="fp64",
+               R=R if not tensor else 8, stream=stream.cuda_stream, device=local).assemble()
+    if prec != "fp64" or tensor:
+        s.replan(prec, R)
     t_asm = time.time() - t0
     esz = 8 if prec == "fp64" else 4
     work_bytes = s.timing()["history_bytes"]
@@ -502,9 +546,6 @@ def run_ours(args, w):
     barrier()
     e1 = time.perf_counter()
     e2e = ws * args.steps / (e1 - e0)
-    batched = None
-    if R > 1 and prec in ("bf16x3", "fp16x3"):
-        batched = batched_vs_plain(s, w, host_out, value / ws, stream, args)
     # roofline of the dominant kernel (history sum: streams every history and right-hand-side block)
     pk = peaks()
     h_ms = statistics.mean(hist_ms) if hist_ms and hist_ms[0] > 0 else None
@@ -531,23 +572,29 @@ def run_ours(args, w):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                      "frac": (achieved / pk["hbm_gbs"]) if achieved else None, "traffic": traffic,
                      "kernel": ("history sum (k_history + k_reduce)" if prec in ("fp64", "fp32") else
-                                "tcgen05 split-precision history GEMM (k_umma_bf16x3 + k_fixup)"),
-                     "algorithmic_bytes_per_launch": work_bytes,
+                                "tcgen05 split-precision history GEMM (k_tc_gemm, fixup in-kernel)"),
+                     "algorithmic_bytes_per_launch": work_bytes, "history_ms": h_ms,
                      "peak_source": "measured" if not pk.get("fallback") else "fallback"},
         "clocks": clk.summary(),
     }
-    if batched:
-        line["batched_vs_plain"] = batched
-    acc = os.path.join(ROOT, "profiles", f"accuracy_{w['name']}.json")
-    if os.path.exists(acc):
-        try:
-            a = json.load(open(acc))["results"].get(prec)
-            if a:
-                line["accuracy"] = {"rel_l2_vs_fp64_path": a["rel_l2_vs_fp64"], "steps": json.load(open(acc))["steps"],
-                                    "waves": 8, "bar": 1e-5, "meets_bar": a["rel_l2_vs_fp64"] <= 1e-5,
-                                    "source": f"profiles/accuracy_{w['name']}.json (bench.py --accuracy)"}
-        except Exception:
-            pass
+    if ws == 1 and tensor and not args.no_accuracy:
+        acc = accuracy_in_run(s, w, args.accuracy_steps, stream)
+        line["accuracy"] = acc
+        # batched vs plain: the plain single-wave FP32 march on the same blocks, timed here
+        s.replan("fp32", 1)
+        one = {k: v[:1] for k, v in w["pw"].items()}
+        o1 = torch.empty((args.steps, 1, s.ne), dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            s.set_excitation(one)
+            s.step(args.warmup)
+            s.step(args.steps, o1)
+            torch.cuda.synchronize()
+        plain = 1e3 / s.timing()["step_ms"]
+        line["batched_vs_plain"] = {
+            "plain": "FP32 history sum, R = 1 (one incident wave per march), same blocks", "plain_steps_s": plain,
+            "batched_wave_steps_s": value / ws * R, "speedup_per_wave": value / ws * R / plain,
+            "rel_l2_batched_vs_fp64": acc["rel_l2_vs_fp64_path"],
+            "rel_l2_plain_vs_fp64": acc["plain_fp32_rel_l2_vs_fp64_path"]}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n, t_casm = cpu_oracle_rate(w, 4 * args.steps + 50)
         sample = (f"{n} march steps of the same workload (assembly {t_casm:.1f} s untimed)" if t_casm is not None else
@@ -572,19 +619,24 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, help="override the workload's path precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the in-run accuracy check")
+    ap.add_argument("--accuracy-steps", type=int, default=300, help="steps of the in-run accuracy check")
     ap.add_argument("--accuracy", action="store_true",
                     help="full-size accuracy of the reduced-precision paths against the FP64 path")
     ap.add_argument("--train-epochs", type=int, default=4, help="learned-guess training passes (ellipsoid12288)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    if args.workload.startswith("batch_uneven"):
+    if args.workload.startswith("batch_uneven") or args.workload == "batch32":
         from synth import workloads
-        probs = workloads.batch_uneven(int(args.workload[len("batch_uneven"):] or 16))
+        if args.workload == "batch32":
+            probs = workloads.batch32()
+        else:
+            probs = workloads.batch_uneven(int(args.workload[len("batch_uneven"):] or 16))
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the uneven batch is measured against the "
                               "same GPU handles stepped one after another, not against the oracle"}))
             return 0
-        return run_batch(args, probs)
+        return run_batch(args, probs, args.workload)
     w = workload(args.workload, args.precision)
     if args.impl == "reference":
         return run_reference(args, w)

@@ -47,9 +47,17 @@ typedef enum { TDCFIE_FP64 = 0, TDCFIE_FP32 = 1, TDCFIE_BF16X3 = 2, TDCFIE_FP16X
  * GMRES = restarted GMRES on T_0: inner Arnoldi cycles of gmres_restart iterations with the
  * path-precision T_0 and CGS2 orthogonalisation in FP64, outer cycles restart from the true FP64
  * residual until ||b - T_0 y|| <= gmres_tol ||b|| (at most gmres_maxit inner iterations in all).
- * Initial guess: ZERO, PREV (y_{n-1}) or MLP (learned, see tdcfie_mlp_*).  FP64 and FP32 paths. */
+ * Initial guess: ZERO, PREV (y_{n-1}), EXTRAP (cubic extrapolation of y_{n-1..n-4}), or a learned
+ * guess (MLP on top of y_{n-1}, MLP_EXTRAP on top of the extrapolation; see tdcfie_mlp_*); y_i = 0
+ * for i <= 0.  FP64 and FP32 paths. */
 typedef enum { TDCFIE_SOLVE_DIRECT = 0, TDCFIE_SOLVE_GMRES = 1 } tdcfie_solver;
-typedef enum { TDCFIE_GUESS_ZERO = 0, TDCFIE_GUESS_PREV = 1, TDCFIE_GUESS_MLP = 2 } tdcfie_guess;
+typedef enum {
+    TDCFIE_GUESS_ZERO = 0,       /* x0 = 0 */
+    TDCFIE_GUESS_PREV = 1,       /* x0 = y_{n-1} */
+    TDCFIE_GUESS_MLP = 2,        /* x0 = y_{n-1} + s f(x): the learned increment */
+    TDCFIE_GUESS_EXTRAP = 3,     /* x0 = 4 y_{n-1} - 6 y_{n-2} + 4 y_{n-3} - y_{n-4}: cubic extrapolation */
+    TDCFIE_GUESS_MLP_EXTRAP = 4  /* x0 = cubic extrapolation + s f(x): the learned correction to it */
+} tdcfie_guess;
 
 typedef struct {
     int precision;        /* tdcfie_precision, default TDCFIE_FP64 */
@@ -130,8 +138,10 @@ tdcfie_status tdcfie_gmres_stats(tdcfie_t h, int64_t* inner_iterations, int64_t*
 /*
  * Learned initial guess for the GMRES solve (an extension: the paper solves with T_0 directly).
  * For unknown m of right-hand side r at step n the features are x = (y_{n-1}, ..., y_{n-8})_{r,m} / s,
- * s = RMS over edges of y_{n-1} for that r (1 if zero), and the guess is y_{n-1} + s f(x) (the network
- * predicts the increment, so a zero network gives the previous-step guess) with
+ * s = RMS over edges of y_{n-1} for that r (1 if zero), and the guess is base + s f(x), base = y_{n-1}
+ * (TDCFIE_GUESS_MLP) or the cubic extrapolation 4 y_{n-1} - 6 y_{n-2} + 4 y_{n-3} - y_{n-4}
+ * (TDCFIE_GUESS_MLP_EXTRAP): the network predicts the correction to its base, so a zero network
+ * gives the base itself, with
  *   f(x) = w3 . tanh(W2 tanh(W1 x + b1) + b2) + b3,  W1 64 x 8, W2 64 x 64, w3 64.
  * Parameters: 4801 float32 in the order W1 (row-major), b1, W2 (row-major), b2, w3, b3.
  * Samples: X n x 8 float32 features (row-major), Y n float32 targets.
@@ -158,11 +168,12 @@ tdcfie_status tdcfie_mlp_predict(const float* params, const float* X, int64_t n,
 /* Training samples from a stored march: y (DEVICE, nt x R x N_E, float64 for precision
  * TDCFIE_FP64 or float32 for TDCFIE_FP32, as written by tdcfie_step_y).  For t = 8 .. nt-1 (0-based
  * rows of y) and every r, m, sample s = ((t - 8) R + r) N_E + m gets X[s] = (y[t-1] .. y[t-8])_{r,m} / sc
- * and Y[s] = (y[t] - y[t-1])_{r,m} / sc, sc = RMS over edges of y[t-1]_r (1 if zero), FP32 arithmetic: the
- * features the march evaluates before each GMRES solve.  X (DEVICE) holds (nt - 8) R N_E x 8 floats,
- * Y (nt - 8) R N_E.  Needs nt >= 9. */
-tdcfie_status tdcfie_mlp_samples(int precision, const void* y, int64_t nt, int64_t R, int64_t ne, float* X, float* Y,
-                                 void* stream);
+ * and Y[s] = (y[t] - base_t)_{r,m} / sc, sc = RMS over edges of y[t-1]_r (1 if zero), base_t = y[t-1]
+ * (base 0) or 4 y[t-1] - 6 y[t-2] + 4 y[t-3] - y[t-4] (base 1); the difference is formed in the
+ * precision of y: the features the march evaluates before each GMRES solve.  X (DEVICE) holds
+ * (nt - 8) R N_E x 8 floats, Y (nt - 8) R N_E.  Needs nt >= 9. */
+tdcfie_status tdcfie_mlp_samples(int precision, int base, const void* y, int64_t nt, int64_t R, int64_t ne, float* X,
+                                 float* Y, void* stream);
 
 /* Load network parameters (HOST, 4801 floats) into an assembled handle (K - 1 >= 8); they are used
  * while the solver is GMRES with guess TDCFIE_GUESS_MLP.  Synchronous.  Until loaded the weights are
@@ -183,22 +194,33 @@ tdcfie_status tdcfie_set_solver(tdcfie_t h, int solver, int guess, double gmres_
 
 /*
  * Several scatterers marched together (the uneven-batch case; the paper marches one scatterer).
- * A batch captures, at its first step, one CUDA graph that holds one step of every handle, each
- * on its own stream branch; every tdcfie_batch_step then launches that graph once per step, so all
- * handles advance together and their kernels run concurrently.  Each handle keeps its blocks, ring
- * and step counter, and computes exactly what tdcfie_step computes.
+ * Every tdcfie_batch_step advances all handles by one launch of a CUDA graph captured at the first
+ * step, and each handle computes exactly what tdcfie_step computes on it (bit for bit).
+ *   Persistent form, used when every handle is FP32 with one incident wave and the direct solve:
+ *   the graph holds ONE cooperative kernel that walks a work list of all handles' items
+ *   (plane-wave tests, history rows over all blocks, T_0^-1 rows, projector gathers,
+ *   pseudo-inverse rows, post-processing), longest items first, with a bounded grid-wide barrier
+ *   between the six phases.
+ *   Graph-branch form, for any other mix: one step of every handle on its own stream branch.
  *
  * tdcfie_batch_create: handles (host array of n assembled handles on one device, each at most once)
  * are borrowed, not owned: destroy the batch before any of them, and re-create it after
- * tdcfie_replan or tdcfie_set_solver on a member.  Host work only, plus stream/event creation.
+ * tdcfie_replan or tdcfie_set_solver on a member.  Host work plus the work lists' upload.
  * tdcfie_batch_step: every handle must have its excitation set; currents_out is NULL (discard) or a
  * host array of n DEVICE pointers laid out as in tdcfie_step for each handle (entries may be NULL).
  * Synchronous; a member's non-finite current or device timeout is returned with its index.
+ * tdcfie_batch_tune (persistent form): times every candidate launch shape (rows per warp 1/2/4,
+ * 128/256/512 threads per block, 1/2/4 blocks per SM within the occupancy limit) for
+ * steps_per_candidate steps each and keeps the fastest; the candidates march the members, which
+ * are then reset to the start of their march (as tdcfie_set_excitation does).  config (host, 4
+ * int32, may be NULL) receives {persistent 1/0, rows per warp, threads per block, blocks per SM}.
+ * For the graph-branch form it only reports {0, ...}.
  * tdcfie_batch_timing: device time per batch step of the last call and kernel launches per step.
  */
 typedef struct tdcfie_batch_s* tdcfie_batch_t;
 tdcfie_status tdcfie_batch_create(const tdcfie_t* handles, int64_t n, tdcfie_batch_t* out);
 tdcfie_status tdcfie_batch_step(tdcfie_batch_t b, int64_t nsteps, void* const* currents_out);
+tdcfie_status tdcfie_batch_tune(tdcfie_batch_t b, int64_t steps_per_candidate, int32_t* config);
 tdcfie_status tdcfie_batch_timing(tdcfie_batch_t b, double* step_ms, int64_t* launches_per_step);
 tdcfie_status tdcfie_batch_destroy(tdcfie_batch_t b);
 
@@ -264,10 +286,33 @@ tdcfie_status tdcfie_block_gemv(int precision, const void* blocks, int64_t nblk,
 tdcfie_status tdcfie_block_gemv_noalloc(int precision, const void* blocks, int64_t nblk, int64_t n, const void* x,
                                         int64_t R, void* out, void* stream);
 
+/*
+ * The history sum of the MOT recurrence (Sec. IV-B, the sum over k of T_k y_{n-k}) in the split
+ * tensor-core arithmetic of the FP16X3 / BF16X3 paths, for caller-held blocks:
+ *     out[r][i] = sum_{q < nblk} sum_{j < cols} blocks[q][i][j] x[q][r][j]
+ * blocks: DEVICE, nblk x rows x cols float64, row-major; x: DEVICE, nblk x R x cols float64;
+ * out: DEVICE, R x rows float64 (caller-owned).  R must be 64.  The blocks are split into two
+ * 16-bit slices with one power-of-two scale per row, the vectors into three (FP16X3) or two
+ * (BF16X3) slices with one scale per 64-element tile, exactly as inside tdcfie_step; the partial
+ * sums are added in FP64.  1 <= nblk <= 4096, 1 <= rows, cols <= 2^20.  Takes its scratch with
+ * cudaMalloc and frees it before returning; synchronous on `stream` (cudaStream_t, NULL = legacy
+ * default stream).  Errors: TDCFIE_E_ARG, TDCFIE_E_UNSUPPORTED, TDCFIE_E_OOM, TDCFIE_E_CUDA,
+ * TDCFIE_E_TIMEOUT (thread-local message in tdcfie_last_error(NULL)).
+ */
+tdcfie_status tdcfie_tc_gemm(int precision, const double* blocks, int64_t nblk, int64_t rows, int64_t cols,
+                             const double* x, int64_t R, double* out, void* stream);
+
 /* Wall-clock seconds of the phases of the last tdcfie_assemble (host output, 6 values): mesh upload,
  * retarded EFIE quadrature, retarded MFIE quadrature, static quadrature, formation of the blocks
  * (projectors, preconditioner, T_k, inverses), path-precision copies. */
 tdcfie_status tdcfie_assembly_timing(tdcfie_t h, double* seconds);
+
+/* Free the FP64 assembly matrices of an assembled handle (S_k, Phi_k, MM_k, H_k, T_k, the static
+ * matrices, L1, L2, the FP64 T_0^-1) and keep only the current step plan, for batches of large
+ * scatterers whose FP64 assembly would not fit on the device together.  The march is unaffected;
+ * afterwards tdcfie_replan, tdcfie_get_matrix and switching to GMRES (unless its T_0 copy already
+ * exists) return TDCFIE_E_STATE.  Synchronous.  Errors: TDCFIE_E_ARG, TDCFIE_E_STATE, TDCFIE_E_CUDA. */
+tdcfie_status tdcfie_release_assembly(tdcfie_t h);
 
 tdcfie_status tdcfie_destroy(tdcfie_t h);
 

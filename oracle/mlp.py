@@ -2,7 +2,9 @@
 
 The paper has no learned component; this follows the per-unknown guess of the build's workload:
 features of unknown m at step n are its last eight values (y_{n-1..n-8})_m divided by
-s_n = RMS_m (y_{n-1})_m; the network predicts y_{n,m} / s_n.  Network 8 -> 64 -> 64 -> 1, tanh
+s_n = RMS_m (y_{n-1})_m; the network predicts the correction (y_{n,m} - b_{n,m}) / s_n to a base b_n
+(y_{n-1}, or the cubic extrapolation of y_{n-1..n-4}), and the guess is b_{n,m} + s_n f(x) (a zero
+network gives the base).  Network 8 -> 64 -> 64 -> 1, tanh
 on both hidden layers, squared-error loss (1/2N) sum (out - target)^2.
 Parameter vector layout (4801 floats): W1 (64 x 8), b1 (64), W2 (64 x 64), b2 (64), W3 (64), b3 (1).
 """
@@ -48,15 +50,21 @@ def loss_and_grad(theta, X, Y):
     return loss, np.concatenate([g[name].reshape(-1) for name, _ in SIZES])
 
 
-def features(y_hist):
+def extrapolate(y_hist):
+    """Cubic polynomial through y_{n-4} .. y_{n-1} evaluated at step n: 4y1 - 6y2 + 4y3 - y4."""
+    return 4.0 * y_hist[-2] - 6.0 * y_hist[-3] + 4.0 * y_hist[-4] - y_hist[-5]
+
+
+def features(y_hist, base: str = "prev"):
     """y_hist: (9, ne, R) = y_{n-8} .. y_n.  Returns X (ne R, 8) = y_{n-1..n-8}/s_n and the target
-    (y_n - y_{n-1})/s_n: the network predicts the increment, so a zero output is the previous-step
-    guess."""
+    (y_n - b_n)/s_n with the base b_n = y_{n-1} ("prev") or the cubic extrapolation ("extrap"): the
+    network predicts the correction to its base, so a zero output is the base itself."""
     prev = y_hist[-2]                                   # y_{n-1}
     s = np.sqrt(np.mean(prev ** 2, axis=0))             # per right-hand side
     s = np.where(s > 0, s, 1.0)
     X = np.stack([y_hist[-2 - k] / s for k in range(8)], axis=-1)   # (ne, R, 8)
-    Y = (y_hist[-1] - y_hist[-2]) / s
+    b = prev if base == "prev" else extrapolate(y_hist)
+    Y = (y_hist[-1] - b) / s
     return X.reshape(-1, 8), Y.reshape(-1), s
 
 

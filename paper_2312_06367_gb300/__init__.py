@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import BF16X3, FP16X3, FP32, FP64, TdcfieError  # noqa: F401
 
-__all__ = ["Solver", "Batch", "block_gemv", "block_gemv_noalloc", "mlp_grad", "mlp_train", "mlp_predict", "mlp_samples",
+__all__ = ["Solver", "Batch", "block_gemv", "block_gemv_noalloc", "tc_gemm", "mlp_grad", "mlp_train", "mlp_predict", "mlp_samples",
            "FP64", "FP32", "BF16X3", "FP16X3", "TdcfieError"]
 
 
@@ -45,6 +45,24 @@ def block_gemv_noalloc(blocks, x, out, stream=None):
     _lib.check(_lib.load().tdcfie_block_gemv_noalloc(prec, ctypes.c_void_p(blocks.data_ptr()), nblk, n,
                                                      ctypes.c_void_p(x.data_ptr()), R,
                                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s)))
+    return out
+
+
+def tc_gemm(blocks, x, precision=FP16X3, out=None, stream=None):
+    """out[r][i] = sum_q sum_j blocks[q][i][j] x[q][r][j] in the split tensor-core arithmetic of the
+    FP16X3 / BF16X3 paths, through tdcfie_tc_gemm.
+
+    blocks (nblk, rows, cols) and x (nblk, 64, cols): contiguous float64 CUDA tensors; returns
+    (64, rows) float64."""
+    import torch
+    nblk, rows, cols = blocks.shape
+    R = x.shape[1]
+    if out is None:
+        out = torch.empty((R, rows), dtype=torch.float64, device=blocks.device)
+    s = stream if stream is not None else torch.cuda.current_stream(blocks.device).cuda_stream
+    _lib.check(_lib.load().tdcfie_tc_gemm(int(precision), ctypes.c_void_p(blocks.data_ptr()), nblk, rows, cols,
+                                          ctypes.c_void_p(x.data_ptr()), R, ctypes.c_void_p(out.data_ptr()),
+                                          ctypes.c_void_p(s)))
     return out
 
 
@@ -87,21 +105,23 @@ def mlp_predict(params, X, stream=None):
     return out
 
 
-def mlp_samples(y, stream=None):
-    """(X, Y) training samples of a stored march y (nt, R, ne) through tdcfie_mlp_samples."""
+def mlp_samples(y, base: str = "prev", stream=None):
+    """(X, Y) training samples of a stored march y (nt, R, ne) through tdcfie_mlp_samples; the target
+    is the correction to base "prev" (y_{n-1}) or "extrap" (cubic extrapolation)."""
     import torch
     nt, R, ne = y.shape
     ns = (nt - 8) * R * ne
     X = torch.empty((ns, 8), dtype=torch.float32, device=y.device)
     Y = torch.empty(ns, dtype=torch.float32, device=y.device)
     prec = FP64 if y.dtype == torch.float64 else FP32
-    _lib.check(_lib.load().tdcfie_mlp_samples(prec, _vp(y), nt, R, ne, _vp(X), _vp(Y),
+    _lib.check(_lib.load().tdcfie_mlp_samples(prec, {"prev": 0, "extrap": 1}[base], _vp(y), nt, R, ne, _vp(X), _vp(Y),
                                               ctypes.c_void_p(_stream(y, stream))))
     return X, Y
 
 
 _SOLVE = {"direct": _lib.SOLVE_DIRECT, "gmres": _lib.SOLVE_GMRES}
-_GUESS = {"zero": _lib.GUESS_ZERO, "prev": _lib.GUESS_PREV, "mlp": _lib.GUESS_MLP}
+_GUESS = {"zero": _lib.GUESS_ZERO, "prev": _lib.GUESS_PREV, "mlp": _lib.GUESS_MLP, "extrap": _lib.GUESS_EXTRAP,
+          "mlp_extrap": _lib.GUESS_MLP_EXTRAP}
 _PREC = {"fp64": FP64, "fp32": FP32, "bf16x3": BF16X3, "fp16x3": FP16X3}
 
 
@@ -238,6 +258,10 @@ class Solver:
         _lib.check(_lib.load().tdcfie_assembly_timing(self._h, _lib._ptr(out)), self._h)
         return dict(zip(("upload", "retarded_efie", "retarded_mfie", "static", "formation", "plan"), out.tolist()))
 
+    def release_assembly(self):
+        """Free the FP64 assembly matrices; the march keeps working (tdcfie_release_assembly)."""
+        _lib.check(_lib.load().tdcfie_release_assembly(self._h), self._h)
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.load().tdcfie_destroy(self._h)
@@ -273,6 +297,13 @@ class Batch:
         if outs is not None:
             ptrs = (ctypes.c_void_p * len(outs))(*[None if o is None else o.data_ptr() for o in outs])
         _lib.check(_lib.load().tdcfie_batch_step(self._b, int(nsteps), ptrs))
+
+    def tune(self, steps_per_candidate: int = 3):
+        """Measure the persistent kernel's launch shapes and keep the fastest (tdcfie_batch_tune);
+        the members are reset to the start of their march.  Returns the chosen configuration."""
+        cfg = np.zeros(4, dtype=np.int32)
+        _lib.check(_lib.load().tdcfie_batch_tune(self._b, int(steps_per_candidate), _lib._ptr(cfg)))
+        return dict(zip(("persistent", "rows_per_warp", "threads", "blocks_per_sm"), cfg.tolist()))
 
     def timing(self):
         ms, n = ctypes.c_double(), ctypes.c_int64()

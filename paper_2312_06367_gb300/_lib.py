@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libtdcfie.so")
 
 FP64, FP32, BF16X3, FP16X3 = 0, 1, 2, 3
 SOLVE_DIRECT, SOLVE_GMRES = 0, 1
-GUESS_ZERO, GUESS_PREV, GUESS_MLP = 0, 1, 2
+GUESS_ZERO, GUESS_PREV, GUESS_MLP, GUESS_EXTRAP, GUESS_MLP_EXTRAP = 0, 1, 2, 3, 4
 MLP_NPARAM = 4801
 STATUS = {0: "OK", -1: "E_ARG", -2: "E_MESH", -3: "E_OOM", -4: "E_CUDA", -5: "E_NOCONV", -6: "E_TIMEOUT",
           -7: "E_NONFINITE", -8: "E_STATE", -9: "E_UNSUPPORTED"}
@@ -58,17 +58,20 @@ SIGNATURES = [
     ("tdcfie_assembly_timing", _I, [_P, _P]),
     ("tdcfie_block_gemv", _I, [_I, _P, _I64, _I64, _P, _I64, _P, _P]),
     ("tdcfie_block_gemv_noalloc", _I, [_I, _P, _I64, _I64, _P, _I64, _P, _P]),
+    ("tdcfie_tc_gemm", _I, [_I, _P, _I64, _I64, _I64, _P, _I64, _P, _P]),
     ("tdcfie_mlp_grad", _I, [_P, _P, _P, _I64, _P, _P, _P]),
     ("tdcfie_mlp_train", _I, [_P, _P, _P, _I64, _I, _I64, ctypes.c_float, ctypes.c_uint64, _P, _P]),
     ("tdcfie_mlp_predict", _I, [_P, _P, _I64, _P, _P]),
-    ("tdcfie_mlp_samples", _I, [_I, _P, _I64, _I64, _I64, _P, _P, _P]),
+    ("tdcfie_mlp_samples", _I, [_I, _I, _P, _I64, _I64, _I64, _P, _P, _P]),
     ("tdcfie_mlp_load", _I, [_P, _P]),
     ("tdcfie_set_solver", _I, [_P, _I, _I, _D]),
     ("tdcfie_replan", _I, [_P, _I, _I64]),
     ("tdcfie_batch_create", _I, [_P, _I64, _P]),
     ("tdcfie_batch_step", _I, [_P, _I64, _P]),
+    ("tdcfie_batch_tune", _I, [_P, _I64, _P]),
     ("tdcfie_batch_timing", _I, [_P, _P, _P]),
     ("tdcfie_batch_destroy", _I, [_P]),
+    ("tdcfie_release_assembly", _I, [_P]),
     ("tdcfie_destroy", _I, [_P]),
     ("tdcfie_last_error", ctypes.c_char_p, [_P]),
 ]

@@ -5,6 +5,8 @@
 #include <string>
 
 #include "internal.h"
+#include "plan.h"
+#include "umma.h"
 
 namespace tdc {
 tdcfie_status form_operators(tdcfie_t h);
@@ -70,7 +72,7 @@ extern "C" tdcfie_status tdcfie_create(const double* vertices, int64_t nv, const
         return fail(nullptr, TDCFIE_E_UNSUPPORTED, "GMRES runs on the FP64 and FP32 paths");
     if (o.solver == TDCFIE_SOLVE_GMRES && !(o.gmres_tol > 0.0 && o.gmres_tol < 1.0))
         return fail(nullptr, TDCFIE_E_ARG, "gmres_tol must be in (0, 1)");
-    if (o.guess < TDCFIE_GUESS_ZERO || o.guess > TDCFIE_GUESS_MLP) return fail(nullptr, TDCFIE_E_ARG, "bad guess");
+    if (o.guess < TDCFIE_GUESS_ZERO || o.guess > TDCFIE_GUESS_MLP_EXTRAP) return fail(nullptr, TDCFIE_E_ARG, "bad guess");
     tdcfie_t h = new tdcfie_s();
     h->opts = o;
     h->R = o.max_rhs;
@@ -244,6 +246,7 @@ extern "C" tdcfie_status tdcfie_replan(tdcfie_t h, int precision, int64_t max_rh
         return fail(h, TDCFIE_E_UNSUPPORTED, "R must be 64 on the tensor-core paths and 1..8 on FP64/FP32");
     if (precision == TDCFIE_FP64 && !h->formed_fp64)
         return fail(h, TDCFIE_E_UNSUPPORTED, "the FP64 path needs blocks formed in FP64 (assemble with precision FP64)");
+    if (h->released) return fail(h, TDCFIE_E_STATE, "the FP64 assembly was released (tdcfie_release_assembly)");
     if (tensor && h->opts.solver == TDCFIE_SOLVE_GMRES) h->opts.solver = TDCFIE_SOLVE_DIRECT;
     h->opts.precision = precision;
     h->opts.max_rhs = max_rhs;
@@ -260,9 +263,11 @@ extern "C" tdcfie_status tdcfie_set_solver(tdcfie_t h, int solver, int guess, do
     if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
     if (!h->assembled || !h->plan) return fail(h, TDCFIE_E_STATE, "call tdcfie_assemble first");
     if (solver != TDCFIE_SOLVE_DIRECT && solver != TDCFIE_SOLVE_GMRES) return fail(h, TDCFIE_E_ARG, "bad solver");
-    if (guess < TDCFIE_GUESS_ZERO || guess > TDCFIE_GUESS_MLP) return fail(h, TDCFIE_E_ARG, "bad guess");
+    if (guess < TDCFIE_GUESS_ZERO || guess > TDCFIE_GUESS_MLP_EXTRAP) return fail(h, TDCFIE_E_ARG, "bad guess");
     if (solver == TDCFIE_SOLVE_GMRES && !(gmres_tol > 0.0 && gmres_tol < 1.0))
         return fail(h, TDCFIE_E_ARG, "gmres_tol must be in (0, 1)");
+    if (solver == TDCFIE_SOLVE_GMRES && h->released && !h->plan->t0mat)
+        return fail(h, TDCFIE_E_STATE, "the FP64 assembly was released (tdcfie_release_assembly)");
     return plan_set_solver(h, solver, guess, gmres_tol);
 }
 
@@ -323,6 +328,7 @@ extern "C" tdcfie_status tdcfie_bc_table(tdcfie_t h, int64_t* nentries, int32_t*
 extern "C" tdcfie_status tdcfie_get_matrix(tdcfie_t h, int which, int64_t k, double* host_out) {
     if (!h || !host_out) return fail(h, TDCFIE_E_ARG, "NULL argument");
     if (!h->assembled) return fail(h, TDCFIE_E_STATE, "not assembled");
+    if (h->released) return fail(h, TDCFIE_E_STATE, "the FP64 assembly was released (tdcfie_release_assembly)");
     const int64_t ne = h->mesh.ne, NN = ne * ne;
     const double* src = nullptr;
     const bool lagged = which >= 0 && which <= 3;
@@ -373,6 +379,21 @@ extern "C" tdcfie_status tdcfie_assembly_timing(tdcfie_t h, double* seconds) {
     return TDCFIE_OK;
 }
 
+extern "C" tdcfie_status tdcfie_release_assembly(tdcfie_t h) {
+    if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
+    if (!h->assembled || !h->plan) return fail(h, TDCFIE_E_STATE, "call tdcfie_assemble first");
+    CK(cudaStreamSynchronize(h->stream));
+    double** ptrs[] = {&h->S, &h->Phi, &h->MM, &h->Zs, &h->Psi, &h->Mst, &h->G, &h->PS, &h->L1, &h->L2, &h->A, &h->T,
+                       &h->T0inv, &h->H, &h->Zh};
+    for (double** q : ptrs)
+        if (*q) {
+            CK(cudaFree(*q));
+            *q = nullptr;
+        }
+    h->released = true;
+    return TDCFIE_OK;
+}
+
 extern "C" tdcfie_status tdcfie_destroy(tdcfie_t h) {
     if (!h) return TDCFIE_OK;
     free_plan(h);
@@ -390,4 +411,9 @@ extern "C" tdcfie_status tdcfie_destroy(tdcfie_t h) {
 extern "C" const char* tdcfie_last_error(tdcfie_t h) {
     if (h) return h->err.c_str();
     return g_last_error.c_str();
+}
+
+extern "C" tdcfie_status tdcfie_tc_gemm(int precision, const double* blocks, int64_t nblk, int64_t rows, int64_t cols,
+                                        const double* x, int64_t R, double* out, void* stream) {
+    return tc_gemm(precision, blocks, nblk, rows, cols, x, R, out, (cudaStream_t)stream);
 }

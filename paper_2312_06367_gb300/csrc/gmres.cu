@@ -39,7 +39,8 @@ __device__ __forceinline__ bool arnoldi(const GmDev& d, int r) {
 }
 
 // x = initial guess; ||b||^2; state reset; H cleared.  mode 0: zero, 1: y_{n-1} (ring slot
-// (n-1) % ring), 2: the learned guess buffer
+// (n-1) % ring), 2 and 4: the learned guess buffer, 3: cubic extrapolation of y_{n-1..n-4}
+// (y_i = 0 for i <= 0)
 template <typename T>
 __global__ void k_gm_init(GmDev d, const T* __restrict__ b, int mode, const T* __restrict__ ringbuf, int ring,
                           const T* __restrict__ learned, const Ctl* ctl) {
@@ -48,7 +49,7 @@ __global__ void k_gm_init(GmDev d, const T* __restrict__ b, int mode, const T* _
     const int64_t n = ctl->n;
     const T* guess = nullptr;
     if (mode == 1 && n > 1) guess = ringbuf + ((n - 1) % ring) * (int64_t)d.R * d.ne;
-    if (mode == 2 && n > 1) guess = learned;
+    if ((mode == 2 || mode == 4) && n > 1) guess = learned;
     if (i == 0) {
         d.flags[r * NFLAGS + F_DONE] = DONE_OPEN;
         d.flags[r * NFLAGS + F_ST] = ST_RESID;
@@ -61,7 +62,14 @@ __global__ void k_gm_init(GmDev d, const T* __restrict__ b, int mode, const T* _
     if (i < 2 * (d.m + 1)) d.hdot[(int64_t)r * 2 * (d.m + 1) + i] = 0.0;
     if (i >= d.ne) return;
     const double bi = (double)b[(int64_t)r * d.ne + i];
-    d.x[(int64_t)r * d.ne + i] = guess ? (double)guess[(int64_t)r * d.ne + i] : 0.0;
+    double x0 = guess ? (double)guess[(int64_t)r * d.ne + i] : 0.0;
+    if (mode == 3) {
+        const double c[4] = {4.0, -6.0, 4.0, -1.0};
+        x0 = 0.0;
+        for (int k = 1; k <= 4 && k <= ring; ++k)
+            if (n - k >= 1) x0 += c[k - 1] * (double)ringbuf[((n - k) % ring) * (int64_t)d.R * d.ne + (int64_t)r * d.ne + i];
+    }
+    d.x[(int64_t)r * d.ne + i] = x0;
     atomicAdd(d.scal + r * NSCAL + S_BN2, bi * bi);
 }
 
@@ -274,16 +282,20 @@ __global__ void __launch_bounds__(256) k_gm_finish(GmDev d, cudaGraphConditional
     }
 }
 
-// y_n (ring slot n % ring, path type) = x; statistics of the step
+// y_n (ring slot n % ring, path type) = x; statistics of the step; the first step with a solve
+// left above the tolerance is recorded in the step state (returned as TDCFIE_E_NOCONV)
 template <typename T>
-__global__ void k_gm_store(GmDev d, T* __restrict__ ringbuf, int ring, const Ctl* ctl) {
+__global__ void k_gm_store(GmDev d, T* __restrict__ ringbuf, int ring, Ctl* ctl) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     if (i == 0 && r == 0) {
         atomicAdd(d.stats + 1, 1ULL);
         atomicMax(d.stats + 2, d.stats[3]);
         for (int q = 0; q < d.R; ++q)
-            if (fl(d, q, F_DONE) != DONE_CONV) atomicAdd(d.stats + 4, 1ULL);
+            if (fl(d, q, F_DONE) != DONE_CONV) {
+                atomicAdd(d.stats + 4, 1ULL);
+                if (atomicCAS(&ctl->noconv, 0, 1) == 0) ctl->noconv_step = ctl->n;
+            }
     }
     if (i >= d.ne) return;
     T* dst = ringbuf + (ctl->n % ring) * (int64_t)d.R * d.ne;

@@ -90,6 +90,8 @@ struct Ctl {              // device-resident step state read by every kernel of 
     int64_t bad_step;
     int timeout;          // set by a device-side bounded wait that ran out
     void* yout;           // optional y_n output of this call (nullptr: none)
+    int noconv;           // set when a GMRES solve stopped above its tolerance (gmres_maxit reached)
+    int64_t noconv_step;  // the first such step
 };
 }  // namespace tdc
 
@@ -105,6 +107,7 @@ struct tdcfie_s {
     int K = 0;
     bool assembled = false, excited = false;
     bool formed_fp64 = false;   // T_k products formed in FP64 (opts.precision was FP64 at assembly)
+    bool released = false;      // FP64 assembly matrices freed (tdcfie_release_assembly)
     // device mesh
     void* dmesh_buf = nullptr;
     tdc::DevMesh dm{};

@@ -19,139 +19,25 @@
 
 #include "internal.h"
 #include "gmres.h"
+#include "simt.h"
 #include "plan.h"
 #include "umma.h"
 
 namespace tdc {
 
 // ---------------------------------------------------------------- plane-wave tests
-// Per edge m a list of quadrature points with a weighted basis vector: 7 points on each
-// triangle of f_m (degree-5 rule, coefficient w A f_m(x)) for e_m and 3 points on each fine
-// triangle of g_m (degree-2 rule, coefficient w A g_m(x)) for h_m.  Per step and wave r:
-//   e_m = sum_x c(x).p_r env_r(x, t_n),  h_m = sum_x c(x).(k_r x p_r) env_r(x, t_n),
-//   env_r(x, t) = amp_r exp(-((t - k_r.x - t0_r)/width_r)^2).
+// e_m(t_n), h_m(t_n) for every (edge, wave), waves fastest (a warp shares one edge's points)
 template <typename T>
 __global__ void k_rhs(int ne, const double* __restrict__ exc, int R, double dt, const Ctl* ctl,
                       const int* __restrict__ pptr, const T* __restrict__ px, const T* __restrict__ pc,
                       const int* __restrict__ nE, T* __restrict__ E, T* __restrict__ H) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= ne * R) return;
-    const int r = idx % R, mm = idx / R;     // waves fastest: a warp shares one edge's points
-    const double* P = exc + 11 * r;   // k(3) p(3) amp t0 width
-    const T kx = (T)P[0], ky = (T)P[1], kz = (T)P[2], qx = (T)P[3], qy = (T)P[4], qz = (T)P[5];
-    const T amp = (T)P[6], inv_w = (T)(1.0 / P[8]);
-    const T tt = (T)((double)ctl->n * dt - P[7]);
-    const T hx = ky * qz - kz * qy, hy = kz * qx - kx * qz, hz = kx * qy - ky * qx;   // k x p
-    T e = 0, h = 0;
-    const int b = pptr[mm], me = b + nE[mm], end = pptr[mm + 1];
-    for (int q = b; q < end; ++q) {
-        const T x = px[3 * q], y = px[3 * q + 1], z = px[3 * q + 2];
-        const T arg = (tt - (kx * x + ky * y + kz * z)) * inv_w;
-        const T env = amp * exp(-arg * arg);
-        const T cx = pc[3 * q], cy = pc[3 * q + 1], cz = pc[3 * q + 2];
-        if (q < me) e += env * (cx * qx + cy * qy + cz * qz);
-        else h += env * (cx * hx + cy * hy + cz * hz);
-    }
+    const int r = idx % R, mm = idx / R;
+    T e, h;
+    rhs_edge<T>(exc + 11 * r, ctl->n, dt, mm, pptr, px, pc, nE, e, h);
     E[(int64_t)r * ne + mm] = e;
     H[(int64_t)r * ne + mm] = h;
-}
-
-// ---------------------------------------------------------------- multi-block GEMV (SIMT)
-// partial[q][r][i] = sum_j B_q[i][j] x_q[r][j] for one warp per (row i, block q); x_q is e_n, h_n
-// or a ring slot chosen from the device step counter.
-template <typename T> struct Vec2;
-template <> struct Vec2<double> { using type = double2; };
-template <> struct Vec2<float> { using type = float4; };
-
-// Row dot products of one warp: acc[r] = B . x_r.  FP64: plain FP64 accumulation.  FP32: the
-// products and their sums are carried error-free (each product's rounding error from an FMA, each
-// addition's from Knuth's TwoSum), so the result equals the exact dot product of the FP32 inputs to
-// about FP32 precision squared; the lanes are combined in FP64.  The MOT recurrence turns y into the
-// current through (y_n - y_{n-1}) / dtt (Eq. post_processing), which magnifies any per-step error of
-// y by about |y| / |y_n - y_{n-1}|; plain FP32 accumulation over rows of thousands of entries is
-// then far above the reduced-precision bar at small time steps.
-template <typename T, int RMAX>
-struct RowDot {
-    __device__ static void run(const T* __restrict__ B, int ncols, const T* __restrict__ x, int R, int ldx,
-                               double* acc) {
-        const int lane = threadIdx.x & 31;
-        T s[RMAX];
-#pragma unroll
-        for (int r = 0; r < RMAX; ++r) s[r] = 0;
-        for (int j = lane; j < ncols; j += 32) {
-            const T a = B[j];
-#pragma unroll
-            for (int r = 0; r < RMAX; ++r)
-                if (r < R) s[r] += a * x[(int64_t)r * ldx + j];
-        }
-#pragma unroll
-        for (int r = 0; r < RMAX; ++r) {
-            double v = (double)s[r];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            acc[r] = v;
-        }
-    }
-};
-
-__device__ __forceinline__ void ff_add(float& hi, float& lo, float a, float b) {
-    const float p = a * b;
-    const float pe = fmaf(a, b, -p);        // a b = p + pe exactly
-    const float t = hi + p;                  // TwoSum(hi, p) = t + te
-    const float bp = t - hi;
-    const float te = (hi - (t - bp)) + (p - bp);
-    hi = t;
-    lo += te + pe;
-}
-
-template <int RMAX>
-struct RowDot<float, RMAX> {
-    __device__ static void run(const float* __restrict__ B, int ncols, const float* __restrict__ x, int R, int ldx,
-                               double* acc) {
-        const int lane = threadIdx.x & 31;
-        // four independent compensated accumulators per right-hand side (one per float4 component)
-        float hi[RMAX][4], lo[RMAX][4];
-#pragma unroll
-        for (int r = 0; r < RMAX; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) hi[r][c] = lo[r][c] = 0.f;
-        const bool vec = ((ncols | ldx) & 3) == 0 && ((reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(x)) & 15) == 0;
-        if (vec) {
-            const float4* B4 = reinterpret_cast<const float4*>(B);
-            for (int j = lane; j < (ncols >> 2); j += 32) {
-                const float4 a = B4[j];
-#pragma unroll
-                for (int r = 0; r < RMAX; ++r)
-                    if (r < R) {
-                        const float4 v = reinterpret_cast<const float4*>(x + (int64_t)r * ldx)[j];
-                        ff_add(hi[r][0], lo[r][0], a.x, v.x);
-                        ff_add(hi[r][1], lo[r][1], a.y, v.y);
-                        ff_add(hi[r][2], lo[r][2], a.z, v.z);
-                        ff_add(hi[r][3], lo[r][3], a.w, v.w);
-                    }
-            }
-        } else {
-            for (int j = lane; j < ncols; j += 32) {
-                const float a = B[j];
-#pragma unroll
-                for (int r = 0; r < RMAX; ++r)
-                    if (r < R) ff_add(hi[r][0], lo[r][0], a, x[(int64_t)r * ldx + j]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < RMAX; ++r) {
-            double v = 0.0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) v += (double)hi[r][c] + (double)lo[r][c];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            acc[r] = v;
-        }
-    }
-};
-
-template <typename T, int RMAX>
-__device__ __forceinline__ void warp_rows(const T* __restrict__ B, int ncols, const T* __restrict__ x, int R,
-                                          int ldx, double* acc) {
-    RowDot<T, RMAX>::run(B, ncols, x, R, ldx, acc);
 }
 
 // Per-block partial sums of the history, kept in FP64 for every path precision
@@ -289,14 +175,7 @@ __global__ void k_project_in(DevMesh m, int R, int ring, const Ctl* ctl, const T
     const int64_t n = ctl->n;
     const T* yn = ringbuf + (n % ring) * (int64_t)R * m.ne + (int64_t)r * m.ne;
     const T* yp = ringbuf + ((n - 1) % ring) * (int64_t)R * m.ne + (int64_t)r * m.ne;
-    const bool first = (n == 1);
-    double s = 0.0;
-    for (int j = 0; j < 3; ++j) {
-        const int e = m.tedge[3 * c + j];
-        const double w = (1.0 / dtt - 1.0) * (double)yn[e] - (first ? 0.0 : (double)yp[e]) / dtt;
-        s += m.tsign[3 * c + j] * w;
-    }
-    z[(int64_t)r * m.nc + c] = (T)s;
+    z[(int64_t)r * m.nc + c] = (T)project_in_value<T>(m, c, yn, yp, n == 1, dtt);
 }
 
 // j[r][m] = y_n[r][m] + u[r][c+(m)] - u[r][c-(m)]; write to out, check finiteness
@@ -379,22 +258,6 @@ tdcfie_status plan_gmres_stats(tdcfie_t h, long long* out6) {
     return TDCFIE_OK;
 }
 
-// host wrappers used by the tensor-core step (umma.cu)
-void launch_rhs_f32(tdcfie_t h, StepPlan* p, float* E, float* H, cudaStream_t s) {
-    const int ne = p->ne, R = p->R, tb = 256;
-    k_rhs<float><<<(ne * R + tb - 1) / tb, tb, 0, s>>>(ne, h->dexc, R, h->dt, p->ctl, p->pptr, (const float*)p->px,
-                                                        (const float*)p->pc, p->pnE, E, H);
-}
-void launch_project_out_f32(tdcfie_t h, StepPlan* p, const float* yring, int ring, const float* u, cudaStream_t s) {
-    const int tb = 256;
-    k_project_out<float><<<(p->ne * p->R + tb - 1) / tb, tb, 0, s>>>(h->dm, p->R, ring, p->ctl, yring, u);
-}
-void launch_project_in_f32(tdcfie_t h, StepPlan* p, const float* yring, int ring, float* z, cudaStream_t s) {
-    const int tb = 256;
-    k_project_in<float><<<(p->nc * p->R + tb - 1) / tb, tb, 0, s>>>(h->dm, p->R, ring, p->ctl, yring, h->dtt, z);
-}
-void launch_advance(StepPlan* p, cudaStream_t s) { k_advance<<<1, 1, 0, s>>>(p->ctl); }
-
 void free_plan(tdcfie_t h) {
     StepPlan* p = h->plan;
     if (!p) return;
@@ -406,7 +269,7 @@ void free_plan(tdcfie_t h) {
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
     if (p->ev2) cudaEventDestroy(p->ev2);
-    if (p->gemm) destroy_bf16x3(p->gemm);
+    if (p->gemm) destroy_tc(p->gemm);
     if (p->gm) destroy_gmres(p->gm);
     if (p->mlp) destroy_mlp(p->mlp);
     if (p->t0mat) cudaFree(p->t0mat);
@@ -528,7 +391,7 @@ tdcfie_status build_plan(tdcfie_t h) {
     CK(cudaMalloc(&p->z, es * R * nc));
     CK(cudaMalloc(&p->u, es * R * nc));
     if (tensor) {
-        tdcfie_status st = build_bf16x3(h, p);
+        tdcfie_status st = build_tc(h, p);
         if (st != TDCFIE_OK) return st;
     } else {
         CK(cudaMalloc(&p->blocks, es * p->nblk * ne * ne));
@@ -576,7 +439,10 @@ tdcfie_status plan_set_solver(tdcfie_t h, int solver, int guess, double tol) {
     const size_t es = p->esz;
     if (solver == TDCFIE_SOLVE_GMRES && (p->prec == TDCFIE_BF16X3 || p->prec == TDCFIE_FP16X3))
         return fail(h, TDCFIE_E_UNSUPPORTED, "GMRES runs on the FP64 and FP32 paths");
-    if (solver == TDCFIE_SOLVE_GMRES && guess == TDCFIE_GUESS_MLP && p->ring < 8)
+    const bool learned = guess == TDCFIE_GUESS_MLP || guess == TDCFIE_GUESS_MLP_EXTRAP;
+    if (solver == TDCFIE_SOLVE_GMRES && guess == TDCFIE_GUESS_EXTRAP && p->ring < 4)
+        return fail(h, TDCFIE_E_UNSUPPORTED, "the extrapolated guess needs K - 1 >= 4 stored steps");
+    if (solver == TDCFIE_SOLVE_GMRES && learned && p->ring < 8)
         return fail(h, TDCFIE_E_UNSUPPORTED, "the learned guess needs K - 1 >= 8 stored steps");
     h->opts.solver = solver;
     h->opts.guess = guess;
@@ -591,10 +457,11 @@ tdcfie_status plan_set_solver(tdcfie_t h, int solver, int guess, double tol) {
         }
         if (!p->gm) CK(build_gmres(h, p));
         gmres_set_tol(p->gm, tol);
-        if (guess == TDCFIE_GUESS_MLP && !p->mlp) CK(build_mlp(p));
+        if (learned && !p->mlp) CK(build_mlp(p));
     }
     p->gmres_on = solver == TDCFIE_SOLVE_GMRES;
-    p->mlp_on = p->gmres_on && guess == TDCFIE_GUESS_MLP;
+    p->mlp_on = p->gmres_on && learned;
+    p->guess_extrap = guess == TDCFIE_GUESS_MLP_EXTRAP;
     if (p->exec) { cudaGraphExecDestroy(p->exec); p->exec = nullptr; }
     if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
     p->nodeA = p->nodeB = nullptr;
@@ -608,7 +475,7 @@ tdcfie_status plan_reset(tdcfie_t h) {
     if (p->gm) CK(reset_gmres_stats(p->gm));
     CK(cudaMemcpyAsync(p->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(p->ringbuf, 0, p->esz * p->ring * p->R * p->ne, s));
-    if (p->gemm) CK(reset_bf16x3(p->gemm, p->ring, s));
+    if (p->gemm) CK(reset_tc(p->gemm, p->ring, p->ne, s));
     CK(cudaStreamSynchronize(s));
     return TDCFIE_OK;
 }
@@ -618,7 +485,7 @@ cudaError_t capture_step(tdcfie_t h, cudaStream_t s) {
     StepPlan* p = h->plan;
     if (p->prec == TDCFIE_FP64) return launch_step<double>(h, *p, s);
     if (p->prec == TDCFIE_FP32) return launch_step<float>(h, *p, s);
-    launch_step_bf16x3(h, p, s);
+    launch_step_tc(h, p, s);
     return cudaGetLastError();
 }
 
@@ -637,16 +504,25 @@ tdcfie_status plan_set_outputs(tdcfie_t h, void* out, void* yout) {
     return TDCFIE_OK;
 }
 
+// Status of the step state words: device timeout, then a non-finite current, then a GMRES solve that
+// stopped above its tolerance (each with the first step it happened at)
+static tdcfie_status status_of(tdcfie_t h, const Ctl& c) {
+    if (c.timeout)
+        return fail(h, TDCFIE_E_TIMEOUT, "a bounded device-side wait ran out (tensor-core pipeline)");
+    if (c.status != 0)
+        return fail(h, TDCFIE_E_NONFINITE, "non-finite current at step " + std::to_string(c.bad_step));
+    if (c.noconv)
+        return fail(h, TDCFIE_E_NOCONV, "GMRES stopped above gmres_tol (gmres_maxit reached) at step " +
+                                            std::to_string(c.noconv_step));
+    return TDCFIE_OK;
+}
+
 // Status words of the last steps of h (call after they completed)
 tdcfie_status plan_check(tdcfie_t h) {
     StepPlan* p = h->plan;
     Ctl c;
     CK(cudaMemcpy(&c, p->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-    if (c.timeout)
-        return fail(h, TDCFIE_E_TIMEOUT, "a bounded device-side wait ran out (tensor-core pipeline)");
-    if (c.status != 0)
-        return fail(h, TDCFIE_E_NONFINITE, "non-finite current at step " + std::to_string(c.bad_step));
-    return TDCFIE_OK;
+    return status_of(h, c);
 }
 
 int plan_launches_per_step(tdcfie_t h) { return h->plan ? h->plan->launches_per_step : 0; }
@@ -665,7 +541,7 @@ tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout) {
         cudaError_t ce = cudaSuccess;
         if (p->prec == TDCFIE_FP64) ce = launch_step<double>(h, *p, s);
         else if (p->prec == TDCFIE_FP32) ce = launch_step<float>(h, *p, s);
-        else launch_step_bf16x3(h, p, s);
+        else launch_step_tc(h, p, s);
         const cudaError_t ee = cudaStreamEndCapture(s, &p->graph);
         if (ce != cudaSuccess) {
             if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
@@ -732,11 +608,7 @@ tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout) {
         CK(gmres_stats(p->gm, g1));
         h->last_launches += (g1[5] - g0[5]) * gmres_body_launches();
     }
-    if (c.timeout)
-        return fail(h, TDCFIE_E_TIMEOUT, "a bounded device-side wait ran out (tensor-core pipeline)");
-    if (c.status != 0)
-        return fail(h, TDCFIE_E_NONFINITE, "non-finite current at step " + std::to_string(c.bad_step));
-    return TDCFIE_OK;
+    return status_of(h, c);
 }
 
 }  // namespace tdc

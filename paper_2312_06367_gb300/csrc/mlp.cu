@@ -183,10 +183,14 @@ __global__ void k_mlp_rms(const T* __restrict__ ringbuf, int ring, int R, int ne
 }
 
 // Training samples from a stored trajectory y (nt x R x ne, step-major): for t = 8 .. nt-1 the
-// sample ((t - 8) R + r) ne + m has X = (y[t-1] .. y[t-8])_{r,m} / s and Y = y[t]_{r,m} / s with
-// s = RMS_m y[t-1]_r.  One block of 256 threads per (t, r).
+// sample ((t - 8) R + r) ne + m has X = (y[t-1] .. y[t-8])_{r,m} / s and the increment target
+// Y = (y[t] - base)_{r,m} / s with s = RMS_m y[t-1]_r, base y[t-1] or the cubic extrapolation
+// 4 y[t-1] - 6 y[t-2] + 4 y[t-3] - y[t-4]; the difference is formed in the
+// trajectory's own precision before the division, so small increments keep their digits.  One
+// block of 256 threads per (t, r).
 template <typename T>
-__global__ void k_mlp_samples(const T* __restrict__ y, int R, int ne, float* __restrict__ X, float* __restrict__ Y) {
+__global__ void k_mlp_samples(const T* __restrict__ y, int R, int ne, int base, float* __restrict__ X,
+                              float* __restrict__ Y) {
     __shared__ float red[256];
     const int64_t q = blockIdx.x;          // (t - 8) * R + r
     const int r = (int)(q % R);
@@ -196,14 +200,17 @@ __global__ void k_mlp_samples(const T* __restrict__ y, int R, int ne, float* __r
     for (int m = threadIdx.x; m < ne; m += blockDim.x) {
         const int64_t o = q * ne + m;
         for (int k = 1; k <= NIN; ++k) X[o * NIN + k - 1] = (float)at(t - k)[m] / s;
-        Y[o] = ((float)at(t)[m] - (float)at(t - 1)[m]) / s;
+        const T b = base ? (T)4 * at(t - 1)[m] - (T)6 * at(t - 2)[m] + (T)4 * at(t - 3)[m] - at(t - 4)[m] : at(t - 1)[m];
+        Y[o] = (float)((at(t)[m] - b) / (T)s);
     }
 }
 
-// guess[r][m] = y_{n-1} + s_r f((y_{n-1..n-8})_{r,m} / s_r); y_i = 0 for i <= 0
+// guess[r][m] = base + s_r f((y_{n-1..n-8})_{r,m} / s_r), base = y_{n-1} or (extrap) the cubic
+// extrapolation 4 y_{n-1} - 6 y_{n-2} + 4 y_{n-3} - y_{n-4}; y_i = 0 for i <= 0.  The base is formed in
+// the path precision T, so a network that outputs zero reproduces it exactly.
 template <typename T>
 __global__ void k_mlp_guess(const __half* __restrict__ wh, const T* __restrict__ ringbuf, int ring, int R, int ne,
-                            const Ctl* ctl, const float* __restrict__ scale, T* __restrict__ guess) {
+                            const Ctl* ctl, const float* __restrict__ scale, int extrap, T* __restrict__ guess) {
     __shared__ float P[NP];
     for (int i = threadIdx.x; i < NP; i += blockDim.x) P[i] = __half2float(wh[i]);
     __syncthreads();
@@ -213,15 +220,18 @@ __global__ void k_mlp_guess(const __half* __restrict__ wh, const T* __restrict__
     const int64_t n = ctl->n;
     const float s = scale[r];
     float x[NIN];
+    T yk[4] = {0, 0, 0, 0};
     for (int k = 1; k <= NIN; ++k) {
-        float v = 0.f;
+        T v = 0;
         if (n - k >= 1) {
             int64_t sl = (n - k) % ring;
-            v = (float)ringbuf[sl * (int64_t)R * ne + (int64_t)r * ne + m];
+            v = ringbuf[sl * (int64_t)R * ne + (int64_t)r * ne + m];
         }
-        x[k - 1] = v / s;
+        if (k <= 4) yk[k - 1] = v;
+        x[k - 1] = (float)v / s;
     }
-    guess[(int64_t)r * ne + m] = (T)(s * (x[0] + mlp_forward(P, x)));   // y_{n-1} + predicted increment
+    const T base = extrap ? (T)4 * yk[0] - (T)6 * yk[1] + (T)4 * yk[2] - yk[3] : yk[0];
+    guess[(int64_t)r * ne + m] = base + (T)(s * mlp_forward(P, x));   // base + predicted correction
 }
 
 // ---------------------------------------------------------------- march integration
@@ -243,7 +253,8 @@ void launch_mlp_guess(StepPlan* p, cudaStream_t s) {
     MlpState* m = p->mlp;
     k_mlp_rms<T><<<p->R, 256, 0, s>>>((const T*)p->ringbuf, p->ring, p->R, p->ne, p->ctl, m->scale);
     k_mlp_guess<T><<<(p->R * p->ne + 127) / 128, 128, 0, s>>>(m->wh, (const T*)p->ringbuf, p->ring, p->R, p->ne,
-                                                                p->ctl, m->scale, (T*)p->guessbuf);
+                                                                p->ctl, m->scale, p->guess_extrap ? 1 : 0,
+                                                                (T*)p->guessbuf);
     p->launches_per_step += 2;
 }
 template void launch_mlp_guess<double>(StepPlan*, cudaStream_t);
@@ -353,18 +364,19 @@ extern "C" tdcfie_status tdcfie_mlp_predict(const float* params, const float* X,
     return e == cudaSuccess ? TDCFIE_OK : cuda_fail(nullptr, e, "MLP predict launch");
 }
 
-extern "C" tdcfie_status tdcfie_mlp_samples(int precision, const void* y, int64_t nt, int64_t R, int64_t ne,
-                                            float* X, float* Y, void* stream) {
+extern "C" tdcfie_status tdcfie_mlp_samples(int precision, int base, const void* y, int64_t nt, int64_t R,
+                                            int64_t ne, float* X, float* Y, void* stream) {
     if (!y || !X || !Y) return fail(nullptr, TDCFIE_E_ARG, "NULL device pointer");
     if (precision != TDCFIE_FP64 && precision != TDCFIE_FP32) return fail(nullptr, TDCFIE_E_ARG, "y is float64 or float32");
+    if (base != 0 && base != 1) return fail(nullptr, TDCFIE_E_ARG, "base is 0 (previous step) or 1 (extrapolation)");
     if (nt < 9 || R < 1 || ne < 1) return fail(nullptr, TDCFIE_E_ARG, "need nt >= 9, R >= 1, ne >= 1");
     if (ne > INT32_MAX || (nt - 8) * R > INT32_MAX) return fail(nullptr, TDCFIE_E_ARG, "sizes out of range");
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned blocks = (unsigned)((nt - 8) * R);
     if (precision == TDCFIE_FP64)
-        k_mlp_samples<double><<<blocks, 256, 0, s>>>((const double*)y, (int)R, (int)ne, X, Y);
+        k_mlp_samples<double><<<blocks, 256, 0, s>>>((const double*)y, (int)R, (int)ne, base, X, Y);
     else
-        k_mlp_samples<float><<<blocks, 256, 0, s>>>((const float*)y, (int)R, (int)ne, X, Y);
+        k_mlp_samples<float><<<blocks, 256, 0, s>>>((const float*)y, (int)R, (int)ne, base, X, Y);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? TDCFIE_OK : cuda_fail(nullptr, e, "MLP sample launch");
 }

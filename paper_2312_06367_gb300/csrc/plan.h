@@ -5,7 +5,7 @@
 #include "internal.h"
 
 namespace tdc {
-struct Bf16x3Gemm;
+struct TcStep;
 struct GmresPlan;
 struct MlpState;
 
@@ -21,6 +21,7 @@ struct StepPlan {
     MlpState* mlp = nullptr;     // learned-guess network (GMRES with TDCFIE_GUESS_MLP)
     bool gmres_on = false;       // per-step solve by GMRES (else the explicit T_0^-1)
     bool mlp_on = false;         // learned guess evaluated each step
+    bool guess_extrap = false;   // learned guess on top of the cubic extrapolation (else y_{n-1})
     void* pinv = nullptr;        // nc x nc
     void* E = nullptr;           // R x ne  (e_n)
     void* Hv = nullptr;          // R x ne  (h_n)
@@ -34,8 +35,8 @@ struct StepPlan {
     Ctl* ctl = nullptr;
     // rhs tables: per edge, quadrature points (x) and weighted basis vectors (c), e-points first
     int* pptr = nullptr; int* pnE = nullptr; void* px = nullptr; void* pc = nullptr;
-    // bf16x3 path
-    Bf16x3Gemm* gemm = nullptr;
+    // tensor-core path
+    TcStep* gemm = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
@@ -46,8 +47,4 @@ struct StepPlan {
 };
 
 
-void launch_rhs_f32(tdcfie_t h, StepPlan* p, float* E, float* H, cudaStream_t s);
-void launch_project_out_f32(tdcfie_t h, StepPlan* p, const float* yring, int ring, const float* u, cudaStream_t s);
-void launch_project_in_f32(tdcfie_t h, StepPlan* p, const float* yring, int ring, float* z, cudaStream_t s);
-void launch_advance(StepPlan* p, cudaStream_t s);
 }  // namespace tdc

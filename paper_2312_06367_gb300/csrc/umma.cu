@@ -2,31 +2,37 @@
 // (tcgen05 + TMEM + TMA), sm_103a.
 //
 // Every matrix-times-block-of-vectors product of a step has the form
-//     out[r][i] = sum_q sum_j A_q[i][j] x_q[r][j]            (r < R right-hand sides)
-// with A_q = A_hi + A_lo and x = x_hi + x_lo split into 16-bit halves (x - hi rounded again).
-// The three products A_hi x_hi + A_hi x_lo + A_lo x_hi are accumulated in FP32 in tensor memory;
-// the lo*lo term is dropped.  Two formats:
-//   BF16X3: bf16 halves, no scaling (about 2^-16 relative per stored entry);
-//   FP16X3: fp16 halves of power-of-two scaled values (row scale per block for A, one scale per
-//           slot and right-hand side for x; about 2^-22 relative per stored entry); the exact
-//           inverse scales are applied in the epilogue.
+//     out[r][i] = sum_q sum_j A_q[i][j] x_q[r][j]            (r < 64 right-hand sides)
+// with the matrix split into two 16-bit slices, A = A_hi + A_lo, and the vectors into XS slices,
+// x = x_hi + x_mid (+ x_lo), each slice the rounded remainder of the previous ones.
+//   FP16X3: fp16 slices of power-of-two scaled values; blocks in two slices (one scale per row of
+//           every block), vectors in three (one scale per 64-element tile of each slot and
+//           right-hand side), about 2^-22 relative per stored matrix entry and 2^-33 per vector
+//           entry.  Five products: A_hi x_hi, A_hi x_mid, A_lo x_hi, A_hi x_lo, A_lo x_mid.
+//   BF16X3: bf16 slices, blocks and vectors in two; three products (hi hi, hi lo, lo hi).
+// Stored matrix errors are fixed perturbations of the operator.  The MOT post-processing
+// differences consecutive y (Eq. post_processing), which magnifies errors that change from step
+// to step (vector rounding, accumulation) by about |y| / |y_n - y_{n-1}|, so those are kept near
+// or below FP32 level: the leading product A_hi x_hi has its own tensor-memory accumulator (D0),
+// separate from the four smaller ones (D1), and each accumulator covers one 64-wide k tile only;
+// the epilogue adds the tiles error-free (TwoSum pairs in registers), partial sums are reduced in
+// FP64 and the results (b_n, y_n, the projector's u) stay in FP64 until they are split again.
 //
-// Kernel layout (one CTA per SM, persistent, 192 threads):
+// Kernel layout (one CTA per SM, persistent, 576 threads):
 //   warp 0   TMA producer: A tiles (128 x 64, 128B swizzle) with L2 evict-first, x tiles
-//            (R x 64) with L2 evict-last, into a STAGES-deep ring of shared-memory stages;
-//   warp 1   one elected thread issues tcgen05.mma (M = 128, N = R, K = 16) and commits each
-//            stage back to the producer and each finished accumulator to the epilogue;
-//   warps 2-5 epilogue: after every chunk (at most CHUNK_KT k tiles of one block q), tcgen05.ld
-//            of the 128 x R FP32 accumulator (two TMEM buffers, so the next chunk's MMAs
-//            overlap), scaling by the block's row and slot scales, error-free accumulation in
-//            registers (hi + lo pairs, TwoSum), and at a row-tile boundary a coalesced store of
-//            the partial sum.  The MOT post-processing differences consecutive y, which magnifies
-//            per-step errors of y about |y| / |y_n - y_{n-1}| times, so a long FP32 chain in
-//            tensor memory would dominate the error at small time steps.
-// Work split: stream-K over (row tile, q, k tile) iterations in row-tile-major order; a CTA's
-// contiguous range covers parts of at most a few row tiles ("segments").  A second kernel sums
-// the segment partials of every row tile in a fixed order (deterministic) and applies the
-// step's epilogue.  Every mbarrier wait is bounded (%globaltimer, 2 s) and reports a timeout.
+//            (64 x 64 per slice) with L2 evict-last, into a 4-deep ring of shared-memory stages;
+//   warp 1   one elected thread issues tcgen05.mma (M = 128, N = 64, K = 16) and commits each
+//            stage back to the producer and each finished pair of accumulators to the epilogue;
+//   warps 2-17 epilogue (one row and 16 right-hand sides per thread): per k tile, tcgen05.ld of D0
+//            and D1 (two TMEM buffers, so the next tile's MMAs overlap), exact power-of-two
+//            rescaling, error-free accumulation, and at the end of the CTA's part of a row tile a
+//            coalesced store of the (hi, lo) partial sums.
+// Work split: stream-K over (row tile, q, k tile) iterations in row-tile-major order.  The CTA
+// that finishes a row tile last (per-tile arrival counter; no waiting) sums every partial of the
+// tile in a fixed order in FP64 and applies the consumer's epilogue: store (u, out), or split into
+// slices for the next product (b_n), or both (y_n: FP64 pair for the post-processing and the
+// slices of the history ring).  Every mbarrier wait is bounded (%globaltimer, 2 s) and reports a
+// timeout.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -41,18 +47,44 @@
 namespace tdc {
 
 constexpr int BM = 128;      // rows per tile (UMMA M)
-constexpr int BK = 64;       // bf16 elements per 128-byte row of a tile
-constexpr int STAGES = 4;
-constexpr int NTHREADS = 192;
+constexpr int BK = 64;       // 16-bit elements per 128-byte row of a tile
+constexpr int NR = 64;       // right-hand sides (UMMA N)
+constexpr int STAGES = 3;
+constexpr int NEPI = 16;                    // epilogue warps: 4 TMEM lane quarters x 4 column groups
+constexpr int NTHREADS = 64 + 32 * NEPI;    // producer warp, MMA warp, epilogue warps
+constexpr int EC = NR / (NEPI / 4);         // columns (right-hand sides) per epilogue warp
+constexpr int FIXR = 4;      // right-hand sides per pass of the row-tile reduction
+#ifndef TDC_D0S
+#define TDC_D0S 1
+#endif
+constexpr int D0S = TDC_D0S;  // accumulators of the leading product per k tile (each 64 / D0S wide in K)
+static_assert(D0S == 1 || D0S == 2 || D0S == 4, "D0S divides the four K = 16 steps of a k tile");
+constexpr int BUFC = (D0S + 1) * NR;                           // TMEM columns of one buffer (D0 parts, D1)
+constexpr int NBUF = BUFC <= 128 ? 4 : (BUFC <= 256 ? 2 : 1);  // accumulator buffers in tensor memory
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
-template <int N>
+template <int XS>
 struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int B_BYTES = N * BK * 2;
-    static constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-    static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + 256 /*barriers*/;
-    static constexpr int TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;
+    static constexpr int X_BYTES = NR * BK * 2;
+    static constexpr int STAGE = 2 * A_BYTES + XS * X_BYTES;
+    static constexpr int MISC = 3072;      // barriers, flags, reduction scratch, tile scales
+    static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + MISC;
+    static_assert(SMEM <= 232448, "shared memory per CTA");
+    static constexpr int TMEM_COLS = 512;   // NBUF buffers x (D0 parts, D1)
+};
+
+enum { FIX_PLAIN = 0, FIX_SPLIT = 1, FIX_SOLVE = 2 };
+
+// what the CTA that completes a row tile does with the tile's sums s[r][row]
+struct FixOut {
+    int mode;
+    double* out;          // PLAIN: out[r * ld_out + row]; SOLVE: out[((n % 2) * NR + r) * ld_out + row]
+    int ld_out;
+    uint16_t* xs[3];      // SPLIT/SOLVE: destination slices, each [slots][NR][ld_x]
+    float* sx;            // inverse scales [slots][ld_x / 64][NR]
+    int ld_x;             // multiple of 64
+    int slot_ring;        // 0: slot 0; > 0: slot n % slot_ring
 };
 
 struct GemmArgs {
@@ -60,13 +92,17 @@ struct GemmArgs {
     int nblk, ktiles, rtiles;
     int64_t total;        // rtiles * nblk * ktiles
     int maxseg;
-    int slot_mode;        // 0: history (q=0 -> slot ring, q=1 -> ring+1, q>=2 -> (n-(q-1)) mod ring); 1: slot 0
+    int slot_mode;        // 0: history (q=0 -> ring, q=1 -> ring+1, q>=2 -> (n-(q-1)) mod ring); 1: slot 0; 2: slot q
     int ring;
-    float* partial;       // [grid][maxseg][N][BM]
+    float* partial;       // [grid][maxseg][2][NR][BM]  (hi, lo)
+    int* cnt;             // [rtiles] arrivals of the current launch (reset by the last arrival)
+    const int* seg_ptr;   // [rtiles + 1]
+    const int* seg_slot;  // partial slots of every row tile, in a fixed order
     Ctl* ctl;
     uint32_t idesc;       // instruction descriptor (operand format)
-    const float* sA;      // [nblk][rows] inverse row scales of A (nullptr: 1)
-    const float* sX;      // [slots][N] inverse scales of x (nullptr: 1)
+    const float* sA;      // [rows] inverse row scales of A (one per row, common to all blocks)
+    const float* sX;      // [slots][ktiles][NR] inverse scales of x
+    FixOut fx;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -135,6 +171,14 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// untiled bulk copy global -> shared (16-byte aligned, size a multiple of 16), counted on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
 __device__ __forceinline__ uint64_t sdesc(const void* tile) {
     const uint64_t addr = smem_u32(tile);
@@ -154,7 +198,8 @@ static uint32_t make_idesc(int n, bool bf16) {
 }
 
 __device__ __forceinline__ int slot_of(const GemmArgs& g, int q, int64_t n) {
-    if (g.slot_mode != 0) return 0;
+    if (g.slot_mode == 1) return 0;
+    if (g.slot_mode == 2) return q;
     if (q == 0) return g.ring;
     if (q == 1) return g.ring + 1;
     int64_t sl = (n - (q - 1)) % g.ring;
@@ -191,21 +236,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
           "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(taddr));
 }
+// 32 lanes x 16 columns
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Accumulator chunks: the MMA warp and the epilogue walk the same sequence of chunks, each at most
-// CHUNK_KT k tiles of one (row tile, block q); a chunk never spans two blocks, so the block's row
-// and slot scales apply to the whole chunk.  Short chunks keep the FP32 accumulation chain in
-// tensor memory short; the epilogue sums the chunks error-free (hi + lo pairs and TwoSum).
-constexpr int CHUNK_KT = 2;
-
-__device__ __forceinline__ int64_t chunk_end(int64_t it, int64_t end, int ktiles) {
-    const int64_t kt = it % ktiles;
-    const int64_t qend = it - kt + ktiles;
-    const int64_t cend = it - kt + (kt / CHUNK_KT + 1) * CHUNK_KT;
-    const int64_t e = cend < qend ? cend : qend;
-    return e < end ? e : end;
-}
+// named barrier of the epilogue warps
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory"); }
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
     const float t = hi + v;
@@ -214,19 +257,79 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
     hi = t;
 }
 
+template <bool F16>
+__device__ __forceinline__ uint16_t to16(float v) {
+    if constexpr (F16) return __half_as_ushort(__float2half_rn(v));
+    else return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+template <bool F16>
+__device__ __forceinline__ float from16(uint16_t b) {
+    if constexpr (F16) return __half2float(__ushort_as_half(b));
+    else return __bfloat162float(__ushort_as_bfloat16(b));
+}
+
+// power of two p with m * p in [2^13, 2^14) (1 for m == 0 or not finite): values scaled by p fill
+// fp16 without overflow.  The exponent is clamped to +-100 so that tiny tiles (an incident pulse
+// that has not arrived, FP32 subnormals) cannot produce an infinite scale.
+__device__ __forceinline__ float fill_scale(float m) {
+    if (!(m > 0.f) || !(m < INFINITY)) return 1.f;
+    int e;
+    frexpf(m, &e);             // m = f 2^e, f in [0.5, 1)
+    int k = 14 - e;
+    k = k > 100 ? 100 : (k < -100 ? -100 : k);
+    return ldexpf(1.f, k);
+}
+
+// v (FP64, already scaled) -> XS 16-bit slices, each the rounded remainder of the previous ones
+template <bool F16, int XS>
+__device__ __forceinline__ void split_value(double v, uint16_t* out) {
+#pragma unroll
+    for (int i = 0; i < XS; ++i) {
+        const uint16_t b = to16<F16>((float)v);
+        out[i] = b;
+        v -= (double)from16<F16>(b);
+    }
+}
+
+#ifndef TDC_XHI_BITS
+#define TDC_XHI_BITS 11
+#endif
+// Vector slices: the leading slice keeps XHI significant bits (rounded to nearest), the others
+// carry the remainder.  Fewer leading bits shorten the products A_hi x_hi that share the leading
+// accumulator, so fewer of their bits fall below the tensor core's alignment window.
+constexpr int XHI = TDC_XHI_BITS;
+template <bool F16, int XS>
+__device__ __forceinline__ void split_vector(double v, uint16_t* out) {
+    if constexpr (XHI < 11 && F16 && XS == 3) {
+        int e;
+        const double m = frexp(v, &e);                        // v = m 2^e, |m| in [0.5, 1)
+        const double h = ldexp(rint(ldexp(m, XHI)), e - XHI);  // v to XHI significant bits
+        out[0] = to16<F16>((float)h);
+        split_value<F16, 2>(v - h, out + 1);
+    } else {
+        split_value<F16, XS>(v, out);
+    }
+}
+
 // ---------------------------------------------------------------- the GEMM kernel
-template <int N>
+template <int XS, bool F16>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_umma_bf16x3(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
-                  const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, GemmArgs g) {
-    using C = Cfg<N>;
+    k_tc_gemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+              const __grid_constant__ CUtensorMap tX0, const __grid_constant__ CUtensorMap tX1,
+              const __grid_constant__ CUtensorMap tX2, GemmArgs g) {
+    using C = Cfg<XS>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * C::STAGE);
+    uint8_t* misc = smem + STAGES * C::STAGE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(misc);
     uint64_t* empty = full + STAGES;
-    uint64_t* acc_full = empty + STAGES;     // [2]
-    uint64_t* acc_empty = acc_full + 2;      // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    uint64_t* acc_full = empty + STAGES;     // [NBUF]
+    uint64_t* acc_empty = acc_full + NBUF;   // [NBUF]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + NBUF);
+    int* last_flag = reinterpret_cast<int*>(tmem_slot + 1);
+    float* red = reinterpret_cast<float*>(misc + 256);    // [NEPI / 4 column groups][4 quads][FIXR] tile maxima
+    float* sx_stage = reinterpret_cast<float*>(misc + 1024);             // [STAGES][NR] x scales of a stage
+    float* sx_buf = reinterpret_cast<float*>(misc + 1024 + STAGES * NR * 4);   // [NBUF][NR] of an accumulator
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int64_t ipt = (int64_t)g.nblk * g.ktiles;     // iterations per row tile
@@ -236,7 +339,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(acc_full + b, 1); mbar_init(acc_empty + b, 128); }
+        // acc_full: the MMA commit and the MMA thread's copy of the tile's x scales
+        for (int b = 0; b < NBUF; ++b) { mbar_init(acc_full + b, 2); mbar_init(acc_empty + b, 32 * NEPI); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -263,11 +367,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int slot = slot_of(g, q, n);
                 if (!mbar_wait(empty + stage, phase ^ 1u, ctl)) break;
                 uint8_t* st = smem + stage * C::STAGE;
-                mbar_expect_tx(full + stage, C::STAGE);
+                mbar_expect_tx(full + stage, C::STAGE + NR * 4);
+                bulk_load(sx_stage + stage * NR, g.sX + ((int64_t)slot * g.ktiles + kt) * NR, NR * 4, full + stage);
                 tma_load_3d(st, &tAh, kt * BK, rt * BM, q, full + stage, pa);
                 tma_load_3d(st + C::A_BYTES, &tAl, kt * BK, rt * BM, q, full + stage, pa);
-                tma_load_3d(st + 2 * C::A_BYTES, &tBh, kt * BK, 0, slot, full + stage, pb);
-                tma_load_3d(st + 2 * C::A_BYTES + C::B_BYTES, &tBl, kt * BK, 0, slot, full + stage, pb);
+                uint8_t* xt = st + 2 * C::A_BYTES;
+                tma_load_3d(xt, &tX0, kt * BK, 0, slot, full + stage, pb);
+                tma_load_3d(xt + C::X_BYTES, &tX1, kt * BK, 0, slot, full + stage, pb);
+                if constexpr (XS == 3) tma_load_3d(xt + 2 * C::X_BYTES, &tX2, kt * BK, 0, slot, full + stage, pb);
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
         }
@@ -276,79 +383,172 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint32_t id = g.idesc;
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t ephase[2] = {0u, 0u};
-            int chunk = 0;
-            bool ok = true;
-            // one accumulator per chunk (at most CHUNK_KT k tiles of one row tile and block q)
-            for (int64_t it = begin; it < end && ok; ++chunk) {
-                const int64_t cend = chunk_end(it, end, g.ktiles);
-                const int buf = chunk & 1;
-                if (!mbar_wait(acc_empty + buf, ephase[buf] ^ 1u, ctl)) { ok = false; break; }
-                ephase[buf] ^= 1u;
+            uint32_t ephase = 0;   // bit b: phase parity of accumulator buffer b
+            int buf = 0;
+            // one accumulator pair per k tile: D0 = A_hi x_hi, D1 = the smaller products
+            for (int64_t it = begin; it < end; ++it) {
+                if (!mbar_wait(acc_empty + buf, ((ephase >> buf) & 1u) ^ 1u, ctl)) break;
+                ephase ^= 1u << buf;
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(buf * N);
-                uint32_t acc = 0;
-                for (; it < cend; ++it) {
-                    if (!mbar_wait(full + stage, phase, ctl)) { ok = false; break; }
-                    tc_fence_after();
-                    uint8_t* st = smem + stage * C::STAGE;
-                    const uint64_t ah = sdesc(st), al = sdesc(st + C::A_BYTES);
-                    const uint64_t bh = sdesc(st + 2 * C::A_BYTES), bl = sdesc(st + 2 * C::A_BYTES + C::B_BYTES);
+                const uint32_t d0 = tmem + (uint32_t)(buf * BUFC), d1 = d0 + D0S * NR;
+                if (!mbar_wait(full + stage, phase, ctl)) break;
+                tc_fence_after();
+                uint8_t* st = smem + stage * C::STAGE;
+                const uint64_t ah = sdesc(st), al = sdesc(st + C::A_BYTES);
+                const uint64_t x0 = sdesc(st + 2 * C::A_BYTES), x1 = sdesc(st + 2 * C::A_BYTES + C::X_BYTES);
+                const uint64_t x2 = sdesc(st + 2 * C::A_BYTES + 2 * C::X_BYTES);
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k) {
-                        const uint64_t adv = (uint64_t)(k * 32) >> 4;   // 16 elements = 32 bytes along K
-                        umma(d, ah + adv, bh + adv, id, acc);
-                        acc = 1;
-                        umma(d, ah + adv, bl + adv, id, 1);
-                        umma(d, al + adv, bh + adv, id, 1);
+                for (int k = 0; k < BK / 16; ++k) {
+                    const uint64_t adv = (uint64_t)(k * 32) >> 4;   // 16 elements = 32 bytes along K
+                    const uint32_t acc = k > 0 ? 1u : 0u;
+                    constexpr int KPER = (BK / 16) / D0S;     // K = 16 steps per leading accumulator
+                    umma(d0 + (uint32_t)((k / KPER) * NR), ah + adv, x0 + adv, id, (k % KPER) ? 1u : 0u);
+                    umma(d1, ah + adv, x1 + adv, id, acc);
+                    umma(d1, al + adv, x0 + adv, id, 1);
+                    if constexpr (XS == 3) {
+                        umma(d1, ah + adv, x2 + adv, id, 1);
+                        umma(d1, al + adv, x1 + adv, id, 1);
                     }
-                    umma_commit(empty + stage);
-                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 }
-                if (!ok) break;
+                {   // the tile's x scales follow its accumulator (the stage is released below)
+                    const float4* src = reinterpret_cast<const float4*>(sx_stage + stage * NR);
+                    float4* dst = reinterpret_cast<float4*>(sx_buf + buf * NR);
+#pragma unroll
+                    for (int c = 0; c < NR / 4; ++c) dst[c] = src[c];
+                }
+                umma_commit(empty + stage);
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 umma_commit(acc_full + buf);
+                mbar_arrive(acc_full + buf);
+                buf = buf + 1 == NBUF ? 0 : buf + 1;
             }
         }
     } else {
-        // epilogue warpgroup: warp w reads TMEM lanes 32 (w % 4) .. + 31 (one row per thread)
-        const int quad = warp & 3;
-        const int row = quad * 32 + lane;
-        uint32_t fphase[2] = {0u, 0u};
-        float acc_hi[N], acc_lo[N];
+        // epilogue: NEPI warps; warp w reads TMEM lanes 32 (w % 4) .. + 31 (one row per thread) and
+        // the EC columns (right-hand sides) of its group ch = (w - 2) / 4
+        const int quad = warp & 3, ch = (warp - 2) >> 2;
+        const int row = quad * 32 + lane, cbase = ch * EC;
+        uint32_t fphase = 0;   // bit b: phase parity of accumulator buffer b
+        float acc_hi[EC], acc_lo[EC];
 #pragma unroll
-        for (int c = 0; c < N; ++c) acc_hi[c] = acc_lo[c] = 0.f;
-        int chunk = 0, seg = 0;
-        for (int64_t it = begin; it < end; ++chunk) {
-            const int64_t cend = chunk_end(it, end, g.ktiles);
+        for (int c = 0; c < EC; ++c) acc_hi[c] = acc_lo[c] = 0.f;
+        int seg = 0, buf = 0;
+        bool ok = true;
+        float sa = 1.f;
+        int64_t sa_rt = -1;
+        for (int64_t it = begin; it < end; ++it) {
             const int64_t rt = it / ipt;
-            const int q = (int)((it - rt * ipt) / g.ktiles);
-            const int buf = chunk & 1;
-            if (!mbar_wait(acc_full + buf, fphase[buf], ctl)) break;
-            fphase[buf] ^= 1u;
-            tc_fence_after();
-            const int grow = (int)rt * BM + row;
-            const float sa = (g.sA && grow < g.rows) ? g.sA[(int64_t)q * g.rows + grow] : 1.f;
-            const float* sx = g.sX ? g.sX + (int64_t)slot_of(g, q, n) * N : nullptr;
+            const int64_t rem = it - rt * ipt;
+            const int q = (int)(rem / g.ktiles), kt = (int)(rem - (int64_t)q * g.ktiles);
+            if (ok && !mbar_wait(acc_full + buf, (fphase >> buf) & 1u, ctl)) ok = false;
+            fphase ^= 1u << buf;
+            if (ok) {
+                tc_fence_after();
+                if (rt != sa_rt) {   // one scale per row for all blocks: reload at a new row tile
+                    const int grow = (int)rt * BM + row;
+                    sa = grow < g.rows ? g.sA[grow] : 1.f;
+                    sa_rt = rt;
+                }
+                const float* sx = sx_buf + buf * NR + cbase;
+                const uint32_t d0 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BUFC + cbase);
 #pragma unroll
-            for (int c0 = 0; c0 < N; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * N + c0), v);
-                tmem_wait_ld();
+                for (int c0 = 0; c0 < EC; c0 += 16) {
+                    uint32_t v0[D0S][16], v1[16];
 #pragma unroll
-                for (int c = 0; c < 32; ++c)   // power-of-two scales: the products are exact
-                    two_sum_acc(acc_hi[c0 + c], acc_lo[c0 + c], __uint_as_float(v[c]) * sa * (sx ? sx[c0 + c] : 1.f));
+                    for (int part = 0; part < D0S; ++part) tmem_ld16(d0 + part * NR + c0, v0[part]);
+                    tmem_ld16(d0 + D0S * NR + c0, v1);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int c = 0; c < 16; c += 4) {
+                        const float4 s4 = *reinterpret_cast<const float4*>(sx + c0 + c);
+                        const float sc[4] = {s4.x * sa, s4.y * sa, s4.z * sa, s4.w * sa};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {   // power-of-two scales: the products are exact
+#pragma unroll
+                            for (int part = 0; part < D0S; ++part)
+                                two_sum_acc(acc_hi[c0 + c + u], acc_lo[c0 + c + u], __uint_as_float(v0[part][c + u]) * sc[u]);
+                            acc_lo[c0 + c + u] += __uint_as_float(v1[c + u]) * sc[u];
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(acc_empty + buf);
             }
-            tc_fence_before();
-            mbar_arrive(acc_empty + buf);
-            it = cend;
-            if (it == end || it % ipt == 0) {   // end of this CTA's part of row tile rt
-                float* dst = g.partial + ((int64_t)blockIdx.x * g.maxseg + seg) * (int64_t)N * BM;
+            buf = buf + 1 == NBUF ? 0 : buf + 1;
+            if (it + 1 == end || (it + 1) % ipt == 0) {   // end of this CTA's part of row tile rt
+                float* dst = g.partial + ((int64_t)blockIdx.x * g.maxseg + seg) * (int64_t)2 * NR * BM;
 #pragma unroll
-                for (int c = 0; c < N; ++c) {
-                    dst[(int64_t)c * BM + row] = acc_hi[c] + acc_lo[c];
+                for (int c = 0; c < EC; ++c) {
+                    dst[(int64_t)(cbase + c) * BM + row] = acc_hi[c];
+                    dst[(int64_t)(NR + cbase + c) * BM + row] = acc_lo[c];
                     acc_hi[c] = acc_lo[c] = 0.f;
                 }
                 ++seg;
+                __threadfence();
+                epi_sync();
+                if (threadIdx.x == 64) {
+                    const int need = g.seg_ptr[rt + 1] - g.seg_ptr[rt];
+                    const int old = atomicAdd(&g.cnt[rt], 1);
+                    const int last = old == need - 1;
+                    if (last) g.cnt[rt] = 0;     // every arrival of this launch is in
+                    *last_flag = last;
+                    __threadfence();
+                }
+                epi_sync();
+                if (*last_flag) {
+                    // ---- row tile rt complete: FP64 sum of its partials, consumer epilogue
+                    __threadfence();
+                    const FixOut& fx = g.fx;
+                    const int grow = (int)rt * BM + row;
+                    const int half = row >> 6;                       // 64-row half = consumer k tile
+                    const bool split = fx.mode != FIX_PLAIN;
+                    const bool hvalid = split && (int)rt * BM + half * 64 < fx.ld_x;
+                    const int slot = fx.slot_ring > 0 ? (int)(n % fx.slot_ring) : 0;
+                    const int p0 = g.seg_ptr[rt], p1 = g.seg_ptr[rt + 1];
+                    for (int r0 = cbase; r0 < cbase + EC; r0 += FIXR) {
+                        double s[FIXR];
+#pragma unroll
+                        for (int j = 0; j < FIXR; ++j) s[j] = 0.0;
+                        for (int k = p0; k < p1; ++k) {
+                            const float* P = g.partial + (int64_t)g.seg_slot[k] * 2 * NR * BM;
+#pragma unroll
+                            for (int j = 0; j < FIXR; ++j)
+                                s[j] += (double)__ldcg(P + (int64_t)(r0 + j) * BM + row) +
+                                        (double)__ldcg(P + (int64_t)(NR + r0 + j) * BM + row);
+                        }
+                        if (fx.mode != FIX_SPLIT && grow < g.rows) {
+                            double* o = fx.out + (fx.mode == FIX_SOLVE ? (n % 2) * (int64_t)NR * fx.ld_out : 0);
+#pragma unroll
+                            for (int j = 0; j < FIXR; ++j) o[(int64_t)(r0 + j) * fx.ld_out + grow] = s[j];
+                        }
+                        if (split) {
+                            // tile maxima over the 64 rows of each half: warps (2 half, 2 half + 1) of this column half
+#pragma unroll
+                            for (int j = 0; j < FIXR; ++j) {
+                                float m = fabsf((float)s[j]);
+                                if (!(m == m)) m = INFINITY;
+                                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                                if (lane == 0) red[(ch * 4 + quad) * FIXR + j] = m;
+                            }
+                            epi_sync();
+                            if (hvalid) {
+#pragma unroll
+                                for (int j = 0; j < FIXR; ++j) {
+                                    const float mx = fmaxf(red[(ch * 4 + 2 * half) * FIXR + j], red[(ch * 4 + 2 * half + 1) * FIXR + j]);
+                                    const float sc = fill_scale(mx);
+                                    uint16_t sl[3];
+                                    split_vector<F16, XS>(s[j] * (double)sc, sl);
+                                    const int64_t off = ((int64_t)slot * NR + r0 + j) * fx.ld_x + grow;
+#pragma unroll
+                                    for (int i = 0; i < XS; ++i) fx.xs[i][off] = sl[i];
+                                    if ((row & 63) == 0)
+                                        fx.sx[((int64_t)slot * (fx.ld_x / 64) + (rt * 2 + half)) * NR + r0 + j] = 1.f / sc;
+                                }
+                            }
+                            epi_sync();
+                        }
+                    }
+                }
             }
         }
     }
@@ -361,81 +561,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-// ---------------------------------------------------------------- partial-sum reduction + splits
-// For row tile t, seg_ptr[t]..seg_ptr[t+1] lists the partial slots (cta * maxseg + seg) in a fixed
-// order; out[r][row] (+ (n % 2) * R * rows when two_slots) receives their sum in FP32.
-__global__ void k_fixup(const float* __restrict__ partial, const int* __restrict__ seg_ptr,
-                        const int* __restrict__ seg_slot, int rows, int R, const Ctl* ctl, float* __restrict__ out,
-                        int two_slots) {
-    // grid (row tiles, R), BM threads: thread i sums the partials of row t*BM+i, right-hand side r
-    const int t = blockIdx.x, r = blockIdx.y, i = threadIdx.x;
-    const int row = t * BM + i;
-    if (row >= rows) return;
-    float* o = out + (two_slots ? (ctl->n % 2) * (int64_t)R * rows : 0);
-    float s = 0.f;
-    for (int k = seg_ptr[t]; k < seg_ptr[t + 1]; ++k) s += partial[(int64_t)seg_slot[k] * R * BM + (int64_t)r * BM + i];
-    o[(int64_t)r * rows + row] = s;
-}
-
-__device__ __forceinline__ uint16_t to16(float v, bool fp16) {
-    return fp16 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16_rn(v));
-}
-__device__ __forceinline__ float from16(uint16_t b, bool fp16) {
-    return fp16 ? __half2float(__ushort_as_half(b)) : __bfloat162float(__ushort_as_bfloat16(b));
-}
-
-// power of two p with m * p in (2^13, 2^14] (1 for m == 0): values scaled by p fill fp16 safely.
-// The exponent is clamped to +-100 so that tiny vectors (e.g. an incident pulse that has passed,
-// FP32 subnormals) cannot produce an infinite scale; such values then round to zero in fp16.
-__device__ __forceinline__ float fill_scale(float m) {
-    if (!(m > 0.f)) return 1.f;
-    int e;
-    frexpf(m, &e);             // m = f 2^e, f in [0.5, 1)
-    int k = 14 - e;
-    k = k > 100 ? 100 : (k < -100 ? -100 : k);
-    return ldexpf(1.f, k);
-}
-
-// x: FP32 [R][n] (slot (n_step % 2) of a pair when pair != 0) -> 16-bit hi/lo [R][ld] into slot
-// `slot` (slot < 0: n_step % ring) with one scale per right-hand side.  Grid (chunks, R): every
-// block reduces the whole vector r to its maximum (cheap, from L2) and writes its chunk.
-constexpr int SPLIT_CHUNK = 1024;
-__global__ void k_split_vec(const float* __restrict__ x, int n, int R, int ld, uint16_t* __restrict__ hi,
-                            uint16_t* __restrict__ lo, float* __restrict__ inv_scale, int slot, int ring, int pair,
-                            int fp16, const Ctl* ctl) {
-    __shared__ float red[256];
-    const int r = blockIdx.y;
-    const int64_t step = ctl->n;
-    const float* xr = x + (pair ? (step % 2) * (int64_t)R * n : 0) + (int64_t)r * n;
-    const int sl = slot >= 0 ? slot : (int)(step % ring);
-    float sc = 1.f;
-    if (fp16) {
-        float m = 0.f;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(xr[i]));
-        red[threadIdx.x] = m;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
-            __syncthreads();
-        }
-        sc = fill_scale(red[0]);
-    }
-    const int64_t off = (int64_t)sl * R * ld + (int64_t)r * ld;
-    const int i0 = blockIdx.x * SPLIT_CHUNK, i1 = min(n, i0 + SPLIT_CHUNK);
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const float v = xr[i] * sc;
-        const uint16_t h = to16(v, fp16);
-        hi[off + i] = h;
-        lo[off + i] = to16(v - from16(h, fp16), fp16);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && inv_scale) inv_scale[(int64_t)sl * R + r] = 1.f / sc;
-}
-
-// FP64 matrix block (rows x cols, times `scale`) -> 16-bit hi/lo [rows][ld], zero padding;
-// fp16: each row scaled by a power of two (inverse stored in inv_row).  One block per row.
-__global__ void k_split_mat(const double* __restrict__ A, int rows, int cols, int ld, double scale,
-                            uint16_t* __restrict__ hi, uint16_t* __restrict__ lo, float* __restrict__ inv_row,
-                            int fp16) {
+// ---------------------------------------------------------------- operand preparation
+// rowmax[r] = max(rowmax[r], max_c |scale A[r][c]|) (non-negative floats order as their bits).
+// One block per row.
+__global__ void k_row_absmax(const double* __restrict__ A, int rows, int cols, double scale, float* __restrict__ rowmax) {
     __shared__ double red[256];
     const int r = blockIdx.x;
     const double* a = A + (int64_t)r * cols;
@@ -447,14 +576,213 @@ __global__ void k_split_mat(const double* __restrict__ A, int rows, int cols, in
         if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
         __syncthreads();
     }
-    const float sc = fp16 ? fill_scale((float)red[0]) : 1.f;
+    if (threadIdx.x == 0) {
+        float mf = (float)red[0];
+        if (!(mf == mf)) mf = INFINITY;
+        atomicMax(reinterpret_cast<unsigned int*>(rowmax) + r, __float_as_uint(mf));
+    }
+}
+
+// FP64 matrix block (rows x cols, times `scale`) -> 16-bit hi/lo [rows][ld] with zero padding; row r
+// scaled by the power of two of rowmax[r] (the maximum over every block that shares the row
+// scale; its inverse goes to inv_row).  One block per row.
+template <bool F16>
+__global__ void k_split_mat(const double* __restrict__ A, int rows, int cols, int ld, double scale,
+                            const float* __restrict__ rowmax, uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
+                            float* __restrict__ inv_row) {
+    const int r = blockIdx.x;
+    const double* a = A + (int64_t)r * cols;
+    const float sc = fill_scale(rowmax[r]);
     for (int c = threadIdx.x; c < ld; c += blockDim.x) {
         const double v = c < cols ? scale * a[c] * (double)sc : 0.0;
-        const uint16_t h = to16((float)v, fp16);
-        hi[(int64_t)r * ld + c] = h;
-        lo[(int64_t)r * ld + c] = to16((float)(v - (double)from16(h, fp16)), fp16);
+        uint16_t sl[2];
+        split_value<F16, 2>(v, sl);
+        hi[(int64_t)r * ld + c] = sl[0];
+        lo[(int64_t)r * ld + c] = sl[1];
     }
-    if (threadIdx.x == 0 && inv_row) inv_row[r] = 1.f / sc;
+    if (threadIdx.x == 0) inv_row[r] = 1.f / sc;
+}
+
+// FP64 vectors x[q][r][cols] -> XS slices [q][NR][ld] and inverse scales [q][ld/64][NR], one
+// scale per 64-element tile of every vector.  Grid (ld/64, nblk), 256 threads.
+template <bool F16, int XS>
+__global__ void __launch_bounds__(256) k_split_x(const double* __restrict__ x, int cols, int ld, uint16_t* __restrict__ X0,
+                                                 uint16_t* __restrict__ X1, uint16_t* __restrict__ X2,
+                                                 float* __restrict__ sX) {
+    __shared__ double v[NR][65];
+    __shared__ float scl[NR];
+    const int kt = blockIdx.x, q = blockIdx.y, t = threadIdx.x;
+    for (int i = t; i < NR * 64; i += 256) {
+        const int r = i >> 6, c = i & 63, col = kt * 64 + c;
+        v[r][c] = col < cols ? x[((int64_t)q * NR + r) * cols + col] : 0.0;
+    }
+    __syncthreads();
+    if (t < NR) {
+        float m = 0.f;
+        for (int c = 0; c < 64; ++c) m = fmaxf(m, fabsf((float)v[t][c]));
+        scl[t] = fill_scale(m);
+        sX[((int64_t)q * (ld / 64) + kt) * NR + t] = 1.f / scl[t];
+    }
+    __syncthreads();
+    uint16_t* dst[3] = {X0, X1, X2};
+    for (int i = t; i < NR * 64; i += 256) {
+        const int r = i >> 6, c = i & 63;
+        uint16_t sl[3];
+        split_vector<F16, XS>(v[r][c] * (double)scl[r], sl);
+        const int64_t off = ((int64_t)q * NR + r) * ld + kt * 64 + c;
+#pragma unroll
+        for (int k = 0; k < XS; ++k) dst[k][off] = sl[k];
+    }
+}
+
+// ---------------------------------------------------------------- plane-wave tests, split
+// e_m(t_n) = sum_x c(x).p_r env_r(x, t_n), h_m(t_n) = sum_x c(x).(k_r x p_r) env_r(x, t_n),
+// env_r(x, t) = amp_r exp(-((t - k_r.x - t0_r)/width_r)^2) (Sec. II-C tests of the incident
+// field).  One block per (64-edge tile, 16 waves): compensated FP32 sums over the quadrature
+// points, then the split into the e (slot ring) and h (slot ring + 1) slices of the history
+// operand with one scale per (slot, tile, wave).  t - t0 is carried as an FP32 pair so that late
+// times lose no digits of the pulse's argument.
+constexpr int RHS_RB = 16;
+template <bool F16, int XS>
+__global__ void __launch_bounds__(256) k_rhs_tc(int ne, const double* __restrict__ exc, double dt, const Ctl* ctl,
+                                                const int* __restrict__ pptr, const float* __restrict__ px,
+                                                const float* __restrict__ pc, const int* __restrict__ nE,
+                                                uint16_t* __restrict__ X0, uint16_t* __restrict__ X1,
+                                                uint16_t* __restrict__ X2, float* __restrict__ sX, int ring, int ld) {
+    __shared__ double ev[2][64][RHS_RB + 1];
+    __shared__ float mred[2][8][RHS_RB];
+    __shared__ float scl[2][RHS_RB];
+    const int tile = blockIdx.x, rb = blockIdx.y * RHS_RB;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int rl = lane & 15, r = rb + rl;
+    const double* P = exc + 11 * r;
+    const float kx = (float)P[0], ky = (float)P[1], kz = (float)P[2], qx = (float)P[3], qy = (float)P[4], qz = (float)P[5];
+    const float amp = (float)P[6], inv_w = (float)(1.0 / P[8]);
+    const double tt = (double)ctl->n * dt - P[7];
+    const float tt_hi = (float)tt, tt_lo = (float)(tt - (double)tt_hi);
+    const float hx = ky * qz - kz * qy, hy = kz * qx - kx * qz, hz = kx * qy - ky * qx;   // k x p
+    float me = 0.f, mh = 0.f;
+    for (int i = 0; i < 4; ++i) {
+        const int el = 2 * warp + (lane >> 4) + 16 * i;     // edge within the tile
+        const int mm = tile * 64 + el;
+        float e_hi = 0.f, e_lo = 0.f, h_hi = 0.f, h_lo = 0.f;
+        if (mm < ne) {
+            const int b = pptr[mm], me_ = b + nE[mm], end = pptr[mm + 1];
+            for (int qp = b; qp < end; ++qp) {
+                const float x = px[3 * qp], y = px[3 * qp + 1], z = px[3 * qp + 2];
+                const float arg = ((tt_hi - fmaf(kx, x, fmaf(ky, y, kz * z))) + tt_lo) * inv_w;
+                const float env = amp * expf(-arg * arg);
+                const float cx = pc[3 * qp], cy = pc[3 * qp + 1], cz = pc[3 * qp + 2];
+                if (qp < me_) two_sum_acc(e_hi, e_lo, env * fmaf(cx, qx, fmaf(cy, qy, cz * qz)));
+                else two_sum_acc(h_hi, h_lo, env * fmaf(cx, hx, fmaf(cy, hy, cz * hz)));
+            }
+        }
+        const double ed = (double)e_hi + (double)e_lo, hd = (double)h_hi + (double)h_lo;
+        ev[0][el][rl] = ed;
+        ev[1][el][rl] = hd;
+        me = fmaxf(me, fabsf((float)ed));
+        mh = fmaxf(mh, fabsf((float)hd));
+    }
+    // per-wave maxima over the 64 edges: lanes l and l + 16 share a wave
+    me = fmaxf(me, __shfl_xor_sync(0xffffffffu, me, 16));
+    mh = fmaxf(mh, __shfl_xor_sync(0xffffffffu, mh, 16));
+    if (lane < 16) { mred[0][warp][lane] = me; mred[1][warp][lane] = mh; }
+    __syncthreads();
+    if (t < 2 * RHS_RB) {
+        const int w = t / RHS_RB, j = t % RHS_RB;
+        float m = 0.f;
+        for (int k = 0; k < 8; ++k) m = fmaxf(m, mred[w][k][j]);
+        if (!(m == m)) m = INFINITY;
+        scl[w][j] = fill_scale(m);
+        sX[((int64_t)(ring + w) * (ld / 64) + tile) * NR + rb + j] = 1.f / scl[w][j];
+    }
+    __syncthreads();
+    uint16_t* dst[3] = {X0, X1, X2};
+    for (int i = t; i < 2 * RHS_RB * 64; i += 256) {
+        const int w = i / (RHS_RB * 64), j = (i / 64) % RHS_RB, el = i & 63;
+        uint16_t sl[3];
+        split_vector<F16, XS>(ev[w][el][j] * (double)scl[w][j], sl);
+        const int64_t off = ((int64_t)(ring + w) * NR + rb + j) * ld + tile * 64 + el;
+#pragma unroll
+        for (int k = 0; k < XS; ++k) dst[k][off] = sl[k];
+    }
+}
+
+// ---------------------------------------------------------------- projector in / out
+// z[r][c] = sum_j tsign[c][j] w[r][tedge[c][j]], w = (1/dtt - 1) y_n - y_{n-1}/dtt, from the FP64
+// pair of the last two y; split into the z slices with one scale per (64-triangle tile, wave).
+template <bool F16, int XS>
+__global__ void __launch_bounds__(256) k_project_in_tc(DevMesh m, const Ctl* ctl, const double* __restrict__ y2,
+                                                       double dtt, uint16_t* __restrict__ Z0, uint16_t* __restrict__ Z1,
+                                                       uint16_t* __restrict__ Z2, float* __restrict__ sZ, int ldc) {
+    __shared__ double zv[RHS_RB][65];
+    __shared__ float scl[RHS_RB];
+    const int tile = blockIdx.x, rb = blockIdx.y * RHS_RB;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int64_t n = ctl->n;
+    const double* yn = y2 + (n % 2) * (int64_t)NR * m.ne;
+    const double* yp = y2 + ((n + 1) % 2) * (int64_t)NR * m.ne;
+    float mx = 0.f;
+    // thread -> (wave rb + (t >> 4) ... ): 16 waves x 64 triangles, 4 per thread, triangles fastest
+    for (int i = t; i < RHS_RB * 64; i += 256) {
+        const int j = i >> 6, cl = i & 63, c = tile * 64 + cl, r = rb + j;
+        double s = 0.0;
+        if (c < m.nc) {
+            for (int k = 0; k < 3; ++k) {
+                const int e = m.tedge[3 * c + k];
+                const double w = (1.0 / dtt - 1.0) * yn[(int64_t)r * m.ne + e] - yp[(int64_t)r * m.ne + e] / dtt;
+                s += m.tsign[3 * c + k] * w;
+            }
+        }
+        zv[j][cl] = s;
+    }
+    __syncthreads();
+    // maxima: warp w covers waves 2w, 2w+1 (lanes 0-15 / 16-31), 4 triangles per lane
+    {
+        const int j = 2 * warp + (lane >> 4), c4 = (lane & 15) * 4;
+        for (int k = 0; k < 4; ++k) mx = fmaxf(mx, fabsf((float)zv[j][c4 + k]));
+        for (int o = 8; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((lane & 15) == 0) {
+            if (!(mx == mx)) mx = INFINITY;
+            scl[j] = fill_scale(mx);
+            sZ[((int64_t)tile) * NR + rb + j] = 1.f / scl[j];
+        }
+    }
+    __syncthreads();
+    uint16_t* dst[3] = {Z0, Z1, Z2};
+    for (int i = t; i < RHS_RB * 64; i += 256) {
+        const int j = i >> 6, cl = i & 63;
+        uint16_t sl[3];
+        split_vector<F16, XS>(zv[j][cl] * (double)scl[j], sl);
+        const int64_t off = (int64_t)(rb + j) * ldc + tile * 64 + cl;
+#pragma unroll
+        for (int k = 0; k < XS; ++k) dst[k][off] = sl[k];
+    }
+}
+
+// j[r][m] = y_n[r][m] + u[r][c+(m)] - u[r][c-(m)] in FP64, stored in FP32; finiteness check; the
+// last block to finish advances the step counter (every block has read n before it arrives).
+__global__ void k_project_out_tc(DevMesh m, int R, Ctl* ctl, const double* __restrict__ y2, const double* __restrict__ u,
+                                 int* __restrict__ done) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = ctl->n;
+    if (idx < m.ne * R) {
+        const int r = idx / m.ne, e = idx % m.ne;
+        const double yv = y2[((n % 2) * R + r) * (int64_t)m.ne + e];
+        const double val = yv + u[(int64_t)r * m.nc + m.cplus_[e]] - u[(int64_t)r * m.nc + m.cminus_[e]];
+        if (!isfinite(val) && atomicCAS(&ctl->status, 0, (int)TDCFIE_E_NONFINITE) == 0) ctl->bad_step = n;
+        if (ctl->out) reinterpret_cast<float*>(ctl->out)[((n - ctl->n0) * R + r) * (int64_t)m.ne + e] = (float)val;
+        if (ctl->yout) reinterpret_cast<float*>(ctl->yout)[((n - ctl->n0) * R + r) * (int64_t)m.ne + e] = (float)yv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1) == (int)gridDim.x - 1) {
+            *done = 0;
+            ctl->n = n + 1;
+            __threadfence();
+        }
+    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -489,70 +817,82 @@ static bool make_map(CUtensorMap* m, void* base, int64_t inner, int64_t rows, in
 }
 
 struct Gemm {
-    CUtensorMap ah, al, bh, bl;
+    CUtensorMap ah, al, x[3];
     GemmArgs a;
     int grid = 0;
     int* seg_ptr = nullptr;
     int* seg_slot = nullptr;
+    int* cnt = nullptr;
 };
 
-struct Bf16x3Gemm {
+struct TcStep {
     bool fp16 = false;
+    int xs = 2;
     int ld = 0, ldc = 0, R = 0, sms = 0;
     uint16_t *Ah = nullptr, *Al = nullptr;          // history blocks [nblk][ne][ld]
     uint16_t *Th = nullptr, *Tl = nullptr;          // T_0^-1
     uint16_t *Ph = nullptr, *Pl = nullptr;          // (Sigma^T Sigma)^+
-    uint16_t *Xh = nullptr, *Xl = nullptr;          // history ring + e_n + h_n slots [ring+2][R][ld]
-    uint16_t *bh = nullptr, *bl = nullptr;          // b [R][ld]
-    uint16_t *zh = nullptr, *zl = nullptr;          // z [R][ldc]
-    float *sAh = nullptr, *sAs = nullptr, *sAp = nullptr;   // inverse row scales (fp16)
-    float *sXh = nullptr, *sXb = nullptr, *sXz = nullptr;   // inverse vector scales (fp16)
-    float *E = nullptr, *H = nullptr, *b32 = nullptr, *y32 = nullptr, *z32 = nullptr, *u32 = nullptr;
+    uint16_t* X[3] = {nullptr, nullptr, nullptr};   // history ring + e_n + h_n slots [ring+2][R][ld]
+    uint16_t* B[3] = {nullptr, nullptr, nullptr};   // b [R][ld]
+    uint16_t* Z[3] = {nullptr, nullptr, nullptr};   // z [R][ldc]
+    float *sAh = nullptr, *sAs = nullptr, *sAp = nullptr;   // inverse row scales
+    float *sXh = nullptr, *sXb = nullptr, *sXz = nullptr;   // inverse tile scales of the vectors
+    double *y2 = nullptr, *u = nullptr;             // FP64 y_n / y_{n-1} pair [2][R][ne], u [R][nc]
+    int* done = nullptr;
     float* partial = nullptr;
     Gemm hist, solve, proj;
     std::vector<void*> owned;
-    ~Bf16x3Gemm() {
+    ~TcStep() {
         for (void* p : owned) cudaFree(p);
         for (Gemm* g : {&hist, &solve, &proj}) {
             if (g->seg_ptr) cudaFree(g->seg_ptr);
             if (g->seg_slot) cudaFree(g->seg_slot);
+            if (g->cnt) cudaFree(g->cnt);
         }
     }
 };
 
-void destroy_bf16x3(Bf16x3Gemm* g) { delete g; }
+void destroy_tc(TcStep* g) { delete g; }
 
-// history ring, e/h slots and the FP32 y pair start at zero (y_i = 0 for i <= 0)
-cudaError_t reset_bf16x3(Bf16x3Gemm* g, int ring, cudaStream_t s) {
+__global__ void k_fill(float* p, int64_t n, float v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
+// history ring, e/h slots and the FP64 y pair start at zero (y_i = 0 for i <= 0)
+cudaError_t reset_tc(TcStep* g, int ring, int ne, cudaStream_t s) {
     const size_t xs = sizeof(uint16_t) * (size_t)(ring + 2) * g->R * g->ld;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(g->Xh, 0, xs, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(g->Xl, 0, xs, s)) != cudaSuccess) return e;
-    return cudaMemsetAsync(g->y32, 0, sizeof(float) * 2 * (size_t)g->R * g->ld, s);
+    for (int i = 0; i < g->xs; ++i)
+        if ((e = cudaMemsetAsync(g->X[i], 0, xs, s)) != cudaSuccess) return e;
+    const int64_t ns = (int64_t)(ring + 2) * (g->ld / 64) * g->R;
+    k_fill<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(g->sXh, ns, 1.f);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaMemsetAsync(g->y2, 0, sizeof(double) * 2 * (size_t)g->R * ne, s);
 }
 
 template <class T>
-static cudaError_t dalloc(Bf16x3Gemm* g, T** p, size_t count) {
+static cudaError_t dalloc(TcStep* g, T** p, size_t count) {
     cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
     if (e == cudaSuccess) g->owned.push_back(*p);
     return e;
 }
 
 // stream-K partition and the per-row-tile list of partial slots (same traversal as the kernel)
-static cudaError_t plan_gemm(Gemm& G, int rows, int cols, int nblk, int sms) {
-    GemmArgs& a = G.a;
+static void plan_segments(GemmArgs& a, int& grid, int rows, int cols, int nblk, int sms, std::vector<int>& ptr,
+                          std::vector<int>& slot) {
     a.rows = rows;
     a.cols = cols;
     a.nblk = nblk;
     a.ktiles = (cols + BK - 1) / BK;
     a.rtiles = (rows + BM - 1) / BM;
     a.total = (int64_t)a.rtiles * nblk * a.ktiles;
-    G.grid = (int)std::min<int64_t>(sms, a.total);
+    grid = (int)std::min<int64_t>(sms, a.total);
     const int64_t ipt = (int64_t)nblk * a.ktiles;
     std::vector<std::vector<std::pair<int, int>>> lists(a.rtiles);
     int maxseg = 1;
-    for (int c = 0; c < G.grid; ++c) {
-        const int64_t b = (int64_t)c * a.total / G.grid, e = (int64_t)(c + 1) * a.total / G.grid;
+    for (int c = 0; c < grid; ++c) {
+        const int64_t b = (int64_t)c * a.total / grid, e = (int64_t)(c + 1) * a.total / grid;
         int seg = 0;
         for (int64_t it = b; it < e; ++seg) {
             const int64_t rt = it / ipt;
@@ -562,30 +902,88 @@ static cudaError_t plan_gemm(Gemm& G, int rows, int cols, int nblk, int sms) {
         maxseg = std::max(maxseg, seg);
     }
     a.maxseg = maxseg;
-    std::vector<int> ptr(a.rtiles + 1, 0), slot;
+    ptr.assign(a.rtiles + 1, 0);
+    slot.clear();
     for (int t = 0; t < a.rtiles; ++t) {
         for (auto& cs : lists[t]) slot.push_back(cs.first * maxseg + cs.second);
         ptr[t + 1] = (int)slot.size();
     }
+}
+
+static cudaError_t plan_gemm(Gemm& G, int rows, int cols, int nblk, int sms) {
+    std::vector<int> ptr, slot;
+    plan_segments(G.a, G.grid, rows, cols, nblk, sms, ptr, slot);
     cudaError_t e;
     if ((e = cudaMalloc(&G.seg_ptr, sizeof(int) * ptr.size())) != cudaSuccess) return e;
     if ((e = cudaMalloc(&G.seg_slot, sizeof(int) * slot.size())) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&G.cnt, sizeof(int) * G.a.rtiles)) != cudaSuccess) return e;
+    if ((e = cudaMemset(G.cnt, 0, sizeof(int) * G.a.rtiles)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(G.seg_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
-    return cudaMemcpy(G.seg_slot, slot.data(), sizeof(int) * slot.size(), cudaMemcpyHostToDevice);
+    if ((e = cudaMemcpy(G.seg_slot, slot.data(), sizeof(int) * slot.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    G.a.seg_ptr = G.seg_ptr;
+    G.a.seg_slot = G.seg_slot;
+    G.a.cnt = G.cnt;
+    return cudaSuccess;
+}
+
+static size_t partial_floats(const Gemm& G) { return (size_t)G.grid * G.a.maxseg * 2 * NR * BM; }
+
+template <int XS, bool F16>
+static void launch_gemm(const Gemm& G, cudaStream_t s) {
+    k_tc_gemm<XS, F16><<<G.grid, NTHREADS, Cfg<XS>::SMEM, s>>>(G.ah, G.al, G.x[0], G.x[1], G.x[2], G.a);
+}
+
+static void run_gemm(const TcStep* g, const Gemm& G, cudaStream_t s) {
+    if (g->fp16) {
+        if (g->xs == 3) launch_gemm<3, true>(G, s);
+        else launch_gemm<2, true>(G, s);
+    } else {
+        launch_gemm<2, false>(G, s);
+    }
+}
+
+static cudaError_t set_smem_attrs() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_tc_gemm<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<3>::SMEM)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_tc_gemm<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<2>::SMEM)) !=
+        cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_tc_gemm<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<2>::SMEM);
+}
+
+// Split a stack of blocks that share one scale per row: maxima over all blocks first
+struct SplitBlock {
+    const double* A;
+    double scale;
+    uint16_t *hi, *lo;
+};
+static cudaError_t split_blocks(bool f16, cudaStream_t s, const std::vector<SplitBlock>& blocks, int rows, int cols,
+                                int ld, float* rowmax, float* inv_row) {
+    cudaError_t e = cudaMemsetAsync(rowmax, 0, sizeof(float) * rows, s);
+    if (e != cudaSuccess) return e;
+    for (const SplitBlock& b : blocks) k_row_absmax<<<rows, 256, 0, s>>>(b.A, rows, cols, b.scale, rowmax);
+    for (const SplitBlock& b : blocks) {
+        if (f16) k_split_mat<true><<<rows, 256, 0, s>>>(b.A, rows, cols, ld, b.scale, rowmax, b.hi, b.lo, inv_row);
+        else k_split_mat<false><<<rows, 256, 0, s>>>(b.A, rows, cols, ld, b.scale, rowmax, b.hi, b.lo, inv_row);
+    }
+    return cudaGetLastError();
 }
 
 #define CKB(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return cuda_fail(h, e_, #x); } while (0)
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-tdcfie_status build_bf16x3(tdcfie_t h, StepPlan* p) {
+tdcfie_status build_tc(tdcfie_t h, StepPlan* p) {
     const int R = p->R, ne = p->ne, nc = p->nc, K = h->K;
-    if (R != 64) return fail(h, TDCFIE_E_UNSUPPORTED, "tensor-core path is built for R = 64 right-hand sides");
+    if (R != NR) return fail(h, TDCFIE_E_UNSUPPORTED, "tensor-core path is built for R = 64 right-hand sides");
     if (!encoder()) return fail(h, TDCFIE_E_CUDA, "cuTensorMapEncodeTiled entry point not available");
-    auto* g = new Bf16x3Gemm();
+    auto* g = new TcStep();
     p->gemm = g;
     g->fp16 = (p->prec == TDCFIE_FP16X3);
-    const int f16 = g->fp16 ? 1 : 0;
+    g->xs = g->fp16 ? 3 : 2;
+    const int XS = g->xs;
     cudaStream_t s = h->stream;
     int dev = 0;
     CKB(cudaGetDevice(&dev));
@@ -601,111 +999,200 @@ tdcfie_status build_bf16x3(tdcfie_t h, StepPlan* p) {
     CKB(dalloc(g, &g->Tl, blk));
     CKB(dalloc(g, &g->Ph, (size_t)nc * ldc));
     CKB(dalloc(g, &g->Pl, (size_t)nc * ldc));
-    CKB(dalloc(g, &g->Xh, (size_t)(ring + 2) * R * ld));
-    CKB(dalloc(g, &g->Xl, (size_t)(ring + 2) * R * ld));
-    CKB(dalloc(g, &g->bh, (size_t)R * ld));
-    CKB(dalloc(g, &g->bl, (size_t)R * ld));
-    CKB(dalloc(g, &g->zh, (size_t)R * ldc));
-    CKB(dalloc(g, &g->zl, (size_t)R * ldc));
-    CKB(dalloc(g, &g->E, (size_t)R * ne));
-    CKB(dalloc(g, &g->H, (size_t)R * ne));
-    CKB(dalloc(g, &g->b32, (size_t)R * ne));
-    CKB(dalloc(g, &g->y32, (size_t)2 * R * ld));
-    CKB(dalloc(g, &g->z32, (size_t)R * nc));
-    CKB(dalloc(g, &g->u32, (size_t)R * nc));
-    if (g->fp16) {
-        CKB(dalloc(g, &g->sAh, (size_t)nblk * ne));
-        CKB(dalloc(g, &g->sAs, (size_t)ne));
-        CKB(dalloc(g, &g->sAp, (size_t)nc));
-        CKB(dalloc(g, &g->sXh, (size_t)(ring + 2) * R));
-        CKB(dalloc(g, &g->sXb, (size_t)R));
-        CKB(dalloc(g, &g->sXz, (size_t)R));
-        std::vector<float> ones((size_t)(ring + 2) * R, 1.f);
-        CKB(cudaMemcpy(g->sXh, ones.data(), sizeof(float) * ones.size(), cudaMemcpyHostToDevice));
+    for (int i = 0; i < XS; ++i) {
+        CKB(dalloc(g, &g->X[i], (size_t)(ring + 2) * R * ld));
+        CKB(dalloc(g, &g->B[i], (size_t)R * ld));
+        CKB(dalloc(g, &g->Z[i], (size_t)R * ldc));
+        CKB(cudaMemsetAsync(g->B[i], 0, sizeof(uint16_t) * R * ld, s));
+        CKB(cudaMemsetAsync(g->Z[i], 0, sizeof(uint16_t) * R * ldc, s));
     }
-    for (void* q : {(void*)g->Xh, (void*)g->Xl}) CKB(cudaMemsetAsync(q, 0, sizeof(uint16_t) * (ring + 2) * R * ld, s));
-    for (void* q : {(void*)g->bh, (void*)g->bl}) CKB(cudaMemsetAsync(q, 0, sizeof(uint16_t) * R * ld, s));
-    for (void* q : {(void*)g->zh, (void*)g->zl}) CKB(cudaMemsetAsync(q, 0, sizeof(uint16_t) * R * ldc, s));
+    for (int i = XS; i < 3; ++i) { g->X[i] = g->X[0]; g->B[i] = g->B[0]; g->Z[i] = g->Z[0]; }   // unused maps
+    CKB(dalloc(g, &g->sAh, (size_t)ne));
+    CKB(dalloc(g, &g->sAs, (size_t)ne));
+    CKB(dalloc(g, &g->sAp, (size_t)nc));
+    float* rowmax = nullptr;
+    CKB(dalloc(g, &rowmax, (size_t)std::max(ne, nc)));
+    CKB(dalloc(g, &g->sXh, (size_t)(ring + 2) * (ld / 64) * R));
+    CKB(dalloc(g, &g->sXb, (size_t)(ld / 64) * R));
+    CKB(dalloc(g, &g->sXz, (size_t)(ldc / 64) * R));
+    CKB(dalloc(g, &g->y2, (size_t)2 * R * ne));
+    CKB(dalloc(g, &g->u, (size_t)R * nc));
+    CKB(dalloc(g, &g->done, 1));
+    CKB(cudaMemsetAsync(g->done, 0, sizeof(int), s));
     // matrices: -A, alpha L2, -T_1 .. -T_{K-1}, then T_0^-1 and the Laplacian pseudo-inverse
     const int64_t NN = (int64_t)ne * ne;
-    auto rows_scale = [&](float* base, int q) { return base ? base + (int64_t)q * ne : nullptr; };
-    k_split_mat<<<ne, 256, 0, s>>>(h->A, ne, ne, ld, -1.0, g->Ah, g->Al, rows_scale(g->sAh, 0), f16);
-    k_split_mat<<<ne, 256, 0, s>>>(h->L2, ne, ne, ld, h->alpha, g->Ah + blk, g->Al + blk, rows_scale(g->sAh, 1), f16);
-    for (int k = 1; k < K; ++k)
-        k_split_mat<<<ne, 256, 0, s>>>(h->T + k * NN, ne, ne, ld, -1.0, g->Ah + (1 + k) * blk, g->Al + (1 + k) * blk,
-                                       rows_scale(g->sAh, 1 + k), f16);
-    k_split_mat<<<ne, 256, 0, s>>>(h->T0inv, ne, ne, ld, 1.0, g->Th, g->Tl, g->sAs, f16);
-    k_split_mat<<<nc, 256, 0, s>>>(h->PinvS, nc, nc, ldc, 1.0, g->Ph, g->Pl, g->sAp, f16);
+    const bool f16 = g->fp16;
+    {
+        std::vector<SplitBlock> hb;
+        hb.push_back({h->A, -1.0, g->Ah, g->Al});
+        hb.push_back({h->L2, h->alpha, g->Ah + blk, g->Al + blk});
+        for (int k = 1; k < K; ++k) hb.push_back({h->T + k * NN, -1.0, g->Ah + (1 + k) * blk, g->Al + (1 + k) * blk});
+        CKB(split_blocks(f16, s, hb, ne, ne, ld, rowmax, g->sAh));
+        CKB(split_blocks(f16, s, {{h->T0inv, 1.0, g->Th, g->Tl}}, ne, ne, ld, rowmax, g->sAs));
+        CKB(split_blocks(f16, s, {{h->PinvS, 1.0, g->Ph, g->Pl}}, nc, nc, ldc, rowmax, g->sAp));
+    }
     CKB(cudaGetLastError());
+    CKB(cudaStreamSynchronize(s));
+    CKB(reset_tc(g, ring, ne, s));
     // GEMM plans and tensor maps
     CKB(plan_gemm(g->hist, ne, ne, nblk, g->sms));
     CKB(plan_gemm(g->solve, ne, ne, 1, g->sms));
     CKB(plan_gemm(g->proj, nc, nc, 1, g->sms));
     size_t pmax = 0;
-    for (Gemm* G : {&g->hist, &g->solve, &g->proj}) pmax = std::max(pmax, (size_t)G->grid * G->a.maxseg * BM * R);
+    for (Gemm* G : {&g->hist, &g->solve, &g->proj}) pmax = std::max(pmax, partial_floats(*G));
     CKB(dalloc(g, &g->partial, pmax));
-    const bool fp = g->fp16;
-    bool ok = make_map(&g->hist.ah, g->Ah, ne, ne, nblk, ld, BM, fp) && make_map(&g->hist.al, g->Al, ne, ne, nblk, ld, BM, fp) &&
-              make_map(&g->hist.bh, g->Xh, ne, R, ring + 2, ld, R, fp) &&
-              make_map(&g->hist.bl, g->Xl, ne, R, ring + 2, ld, R, fp) &&
-              make_map(&g->solve.ah, g->Th, ne, ne, 1, ld, BM, fp) && make_map(&g->solve.al, g->Tl, ne, ne, 1, ld, BM, fp) &&
-              make_map(&g->solve.bh, g->bh, ne, R, 1, ld, R, fp) && make_map(&g->solve.bl, g->bl, ne, R, 1, ld, R, fp) &&
-              make_map(&g->proj.ah, g->Ph, nc, nc, 1, ldc, BM, fp) && make_map(&g->proj.al, g->Pl, nc, nc, 1, ldc, BM, fp) &&
-              make_map(&g->proj.bh, g->zh, nc, R, 1, ldc, R, fp) && make_map(&g->proj.bl, g->zl, nc, R, 1, ldc, R, fp);
+    bool ok = make_map(&g->hist.ah, g->Ah, ne, ne, nblk, ld, BM, f16) && make_map(&g->hist.al, g->Al, ne, ne, nblk, ld, BM, f16) &&
+              make_map(&g->solve.ah, g->Th, ne, ne, 1, ld, BM, f16) && make_map(&g->solve.al, g->Tl, ne, ne, 1, ld, BM, f16) &&
+              make_map(&g->proj.ah, g->Ph, nc, nc, 1, ldc, BM, f16) && make_map(&g->proj.al, g->Pl, nc, nc, 1, ldc, BM, f16);
+    for (int i = 0; i < 3; ++i)
+        ok = ok && make_map(&g->hist.x[i], g->X[i], ne, R, ring + 2, ld, R, f16) &&
+             make_map(&g->solve.x[i], g->B[i], ne, R, 1, ld, R, f16) &&
+             make_map(&g->proj.x[i], g->Z[i], nc, R, 1, ldc, R, f16);
     if (!ok) return fail(h, TDCFIE_E_CUDA, "cuTensorMapEncodeTiled failed");
-    const uint32_t id = make_idesc(R, !fp);
+    const uint32_t id = make_idesc(R, !f16);
     for (Gemm* G : {&g->hist, &g->solve, &g->proj}) {
         G->a.partial = g->partial;
         G->a.ctl = p->ctl;
         G->a.ring = ring;
         G->a.slot_mode = 1;
         G->a.idesc = id;
+        G->a.fx = FixOut{};
     }
+    // history: b_n -> slices of the solve's vector operand
     g->hist.a.slot_mode = 0;
-    g->hist.a.sA = g->sAh; g->hist.a.sX = g->sXh;
-    g->solve.a.sA = g->sAs; g->solve.a.sX = g->sXb;
-    g->proj.a.sA = g->sAp; g->proj.a.sX = g->sXz;
-    CKB(cudaFuncSetAttribute(k_umma_bf16x3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<64>::SMEM));
+    g->hist.a.sA = g->sAh;
+    g->hist.a.sX = g->sXh;
+    g->hist.a.fx.mode = FIX_SPLIT;
+    g->hist.a.fx.ld_x = ld;
+    g->hist.a.fx.sx = g->sXb;
+    for (int i = 0; i < 3; ++i) g->hist.a.fx.xs[i] = g->B[i];
+    // solve: y_n -> FP64 pair (post-processing) and the history ring slot n mod (K - 1)
+    g->solve.a.sA = g->sAs;
+    g->solve.a.sX = g->sXb;
+    g->solve.a.fx.mode = FIX_SOLVE;
+    g->solve.a.fx.out = g->y2;
+    g->solve.a.fx.ld_out = ne;
+    g->solve.a.fx.ld_x = ld;
+    g->solve.a.fx.sx = g->sXh;
+    g->solve.a.fx.slot_ring = ring;
+    for (int i = 0; i < 3; ++i) g->solve.a.fx.xs[i] = g->X[i];
+    // projector: u = (Sigma^T Sigma)^+ z in FP64
+    g->proj.a.sA = g->sAp;
+    g->proj.a.sX = g->sXz;
+    g->proj.a.fx.mode = FIX_PLAIN;
+    g->proj.a.fx.out = g->u;
+    g->proj.a.fx.ld_out = nc;
+    CKB(set_smem_attrs());
     CKB(cudaStreamSynchronize(s));
-    // algorithmic bytes of the history GEMM: every block (hi + lo) once, and its R vectors
-    h->hist_bytes = (double)nblk * ne * ne * 4.0 + (double)nblk * R * ne * 4.0;
+    // algorithmic bytes of the history GEMM: every block (hi + lo) once, and its R vectors (XS slices)
+    h->hist_bytes = (double)nblk * ne * ne * 4.0 + (double)nblk * R * ne * 2.0 * XS;
     return TDCFIE_OK;
 }
 
-static void run_gemm(const Gemm& G, cudaStream_t s) {
-    k_umma_bf16x3<64><<<G.grid, NTHREADS, Cfg<64>::SMEM, s>>>(G.ah, G.al, G.bh, G.bl, G.a);
+void launch_step_tc(tdcfie_t h, StepPlan* p, cudaStream_t s) {
+    TcStep* g = p->gemm;
+    const int R = p->R, ne = p->ne, ring = p->ring, ld = g->ld, ldc = g->ldc;
+    const dim3 grhs(ld / 64, R / RHS_RB), gproj(ldc / 64, R / RHS_RB);
+    // 1. plane-wave tests -> e, h slots of the history operand
+    if (g->fp16)
+        k_rhs_tc<true, 3><<<grhs, 256, 0, s>>>(ne, h->dexc, h->dt, p->ctl, p->pptr, (const float*)p->px,
+                                                (const float*)p->pc, p->pnE, g->X[0], g->X[1], g->X[2], g->sXh, ring, ld);
+    else
+        k_rhs_tc<false, 2><<<grhs, 256, 0, s>>>(ne, h->dexc, h->dt, p->ctl, p->pptr, (const float*)p->px,
+                                                 (const float*)p->pc, p->pnE, g->X[0], g->X[1], g->X[2], g->sXh, ring, ld);
+    // 2. history sum b_n = -A e_n + alpha L2 h_n - sum_k T_k y_{n-k}  (events bracket the GEMM alone)
+    cudaEventRecordWithFlags(p->evA, s, cudaEventRecordExternal);
+    run_gemm(g, g->hist, s);
+    cudaEventRecordWithFlags(p->evB, s, cudaEventRecordExternal);
+    // 3. y_n = T_0^-1 b_n  (FP64 pair slot n % 2; slices into history slot n % ring)
+    run_gemm(g, g->solve, s);
+    // 4. projector: z = Sigma^T w_n, u = (Sigma^T Sigma)^+ z, j_n = y_n + Sigma u
+    if (g->fp16)
+        k_project_in_tc<true, 3><<<gproj, 256, 0, s>>>(h->dm, p->ctl, g->y2, h->dtt, g->Z[0], g->Z[1], g->Z[2], g->sXz, ldc);
+    else
+        k_project_in_tc<false, 2><<<gproj, 256, 0, s>>>(h->dm, p->ctl, g->y2, h->dtt, g->Z[0], g->Z[1], g->Z[2], g->sXz, ldc);
+    run_gemm(g, g->proj, s);
+    k_project_out_tc<<<(ne * R + 255) / 256, 256, 0, s>>>(h->dm, R, p->ctl, g->y2, g->u, g->done);
+    p->launches_per_step = 6;
 }
 
-void launch_step_bf16x3(tdcfie_t h, StepPlan* p, cudaStream_t s) {
-    Bf16x3Gemm* g = p->gemm;
-    const int R = p->R, ne = p->ne, nc = p->nc, ring = p->ring, ld = g->ld, ldc = g->ldc;
-    const int f16 = g->fp16 ? 1 : 0;
-    // plane-wave tests -> e, h slots of the history operand
-    const dim3 gv((ne + SPLIT_CHUNK - 1) / SPLIT_CHUNK, R), gz((nc + SPLIT_CHUNK - 1) / SPLIT_CHUNK, R);
-    launch_rhs_f32(h, p, g->E, g->H, s);
-    k_split_vec<<<gv, 256, 0, s>>>(g->E, ne, R, ld, g->Xh, g->Xl, g->sXh, ring, ring, 0, f16, p->ctl);
-    k_split_vec<<<gv, 256, 0, s>>>(g->H, ne, R, ld, g->Xh, g->Xl, g->sXh, ring + 1, ring, 0, f16, p->ctl);
-    // history sum b_n = -A e_n + alpha L2 h_n - sum_k T_k y_{n-k}  (events bracket the GEMM alone)
-    cudaEventRecordWithFlags(p->evA, s, cudaEventRecordExternal);
-    run_gemm(g->hist, s);
-    cudaEventRecordWithFlags(p->evB, s, cudaEventRecordExternal);
-    k_fixup<<<dim3(g->hist.a.rtiles, R), BM, 0, s>>>(g->partial, g->hist.seg_ptr, g->hist.seg_slot, ne, R, p->ctl,
-                                                     g->b32, 0);
-    k_split_vec<<<gv, 256, 0, s>>>(g->b32, ne, R, ld, g->bh, g->bl, g->sXb, 0, ring, 0, f16, p->ctl);
-    // y_n = T_0^-1 b_n  (FP32 in y32[n % 2]; 16-bit hi/lo into history slot n % ring)
-    run_gemm(g->solve, s);
-    k_fixup<<<dim3(g->solve.a.rtiles, R), BM, 0, s>>>(g->partial, g->solve.seg_ptr, g->solve.seg_slot, ne, R,
-                                                      p->ctl, g->y32, 1);
-    k_split_vec<<<gv, 256, 0, s>>>(g->y32, ne, R, ld, g->Xh, g->Xl, g->sXh, -1, ring, 1, f16, p->ctl);
-    // projector: z = Sigma^T w_n, u = (Sigma^T Sigma)^+ z, j_n = y_n + Sigma u
-    launch_project_in_f32(h, p, g->y32, 2, g->z32, s);
-    k_split_vec<<<gz, 256, 0, s>>>(g->z32, nc, R, ldc, g->zh, g->zl, g->sXz, 0, ring, 0, f16, p->ctl);
-    run_gemm(g->proj, s);
-    k_fixup<<<dim3(g->proj.a.rtiles, R), BM, 0, s>>>(g->partial, g->proj.seg_ptr, g->proj.seg_slot, nc, R, p->ctl,
-                                                     g->u32, 0);
-    launch_project_out_f32(h, p, g->y32, 2, g->u32, s);
-    launch_advance(p, s);
-    p->launches_per_step = 16;
+// ---------------------------------------------------------------- stand-alone product
+// out[r][i] = sum_q sum_j blocks[q][i][j] x[q][r][j] in the split format (see tdcfie.h)
+tdcfie_status tc_gemm(int precision, const double* blocks, int64_t nblk, int64_t rows, int64_t cols, const double* x,
+                      int64_t R, double* out, cudaStream_t s) {
+    tdcfie_t h = nullptr;
+    if (precision != TDCFIE_FP16X3 && precision != TDCFIE_BF16X3)
+        return fail(h, TDCFIE_E_UNSUPPORTED, "tensor-core product supports TDCFIE_FP16X3 and TDCFIE_BF16X3");
+    if (!blocks || !x || !out) return fail(h, TDCFIE_E_ARG, "NULL device pointer");
+    if (R != NR) return fail(h, TDCFIE_E_UNSUPPORTED, "tensor-core product is built for R = 64");
+    if (nblk < 1 || nblk > 4096 || rows < 1 || rows > (1 << 20) || cols < 1 || cols > (1 << 20))
+        return fail(h, TDCFIE_E_ARG, "sizes out of range (1 <= nblk <= 4096, 1 <= rows, cols <= 2^20)");
+    if (!encoder()) return fail(h, TDCFIE_E_CUDA, "cuTensorMapEncodeTiled entry point not available");
+    const bool f16 = precision == TDCFIE_FP16X3;
+    const int XS = f16 ? 3 : 2;
+    const int ld = round_up((int)cols, BK);
+    int dev = 0, sms = 0;
+    CKB(cudaGetDevice(&dev));
+    CKB(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TcStep g;   // owns the scratch below
+    g.fp16 = f16;
+    g.xs = XS;
+    Gemm& G = g.hist;
+    std::vector<int> ptr, slot;
+    plan_segments(G.a, G.grid, (int)rows, (int)cols, (int)nblk, sms, ptr, slot);
+    CKB(dalloc(&g, &g.Ah, (size_t)nblk * rows * ld));
+    CKB(dalloc(&g, &g.Al, (size_t)nblk * rows * ld));
+    CKB(dalloc(&g, &g.sAh, (size_t)rows));
+    float* rowmax = nullptr;
+    CKB(dalloc(&g, &rowmax, (size_t)rows));
+    for (int i = 0; i < XS; ++i) CKB(dalloc(&g, &g.X[i], (size_t)nblk * NR * ld));
+    for (int i = XS; i < 3; ++i) g.X[i] = g.X[0];
+    CKB(dalloc(&g, &g.sXh, (size_t)nblk * (ld / 64) * NR));
+    CKB(dalloc(&g, &g.partial, partial_floats(G)));
+    CKB(dalloc(&g, &G.seg_ptr, ptr.size()));
+    CKB(dalloc(&g, &G.seg_slot, slot.size()));
+    CKB(dalloc(&g, &G.cnt, (size_t)G.a.rtiles));
+    g.owned.erase(g.owned.end() - 3, g.owned.end());   // freed by ~TcStep's per-Gemm loop
+    CKB(cudaMemcpyAsync(G.seg_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, s));
+    CKB(cudaMemcpyAsync(G.seg_slot, slot.data(), sizeof(int) * slot.size(), cudaMemcpyHostToDevice, s));
+    CKB(cudaMemsetAsync(G.cnt, 0, sizeof(int) * G.a.rtiles, s));
+    {
+        std::vector<SplitBlock> sb;
+        for (int64_t q = 0; q < nblk; ++q) sb.push_back({blocks + q * rows * cols, 1.0, g.Ah + q * rows * ld, g.Al + q * rows * ld});
+        CKB(split_blocks(f16, s, sb, (int)rows, (int)cols, ld, rowmax, g.sAh));
+    }
+    const dim3 gx(ld / 64, (unsigned)nblk);
+    if (f16) k_split_x<true, 3><<<gx, 256, 0, s>>>(x, (int)cols, ld, g.X[0], g.X[1], g.X[2], g.sXh);
+    else k_split_x<false, 2><<<gx, 256, 0, s>>>(x, (int)cols, ld, g.X[0], g.X[1], g.X[2], g.sXh);
+    CKB(cudaGetLastError());
+    bool ok = make_map(&G.ah, g.Ah, cols, rows, nblk, ld, BM, f16) && make_map(&G.al, g.Al, cols, rows, nblk, ld, BM, f16);
+    for (int i = 0; i < 3; ++i) ok = ok && make_map(&G.x[i], g.X[i], cols, NR, nblk, ld, NR, f16);
+    if (!ok) return fail(h, TDCFIE_E_CUDA, "cuTensorMapEncodeTiled failed");
+    Ctl* ctl = nullptr;
+    CKB(dalloc(&g, &ctl, 1));
+    CKB(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    G.a.seg_ptr = G.seg_ptr;
+    G.a.seg_slot = G.seg_slot;
+    G.a.cnt = G.cnt;
+    G.a.partial = g.partial;
+    G.a.ctl = ctl;
+    G.a.ring = 1;
+    G.a.slot_mode = 2;
+    G.a.idesc = make_idesc(NR, !f16);
+    G.a.sA = g.sAh;
+    G.a.sX = g.sXh;
+    G.a.fx = FixOut{};
+    G.a.fx.mode = FIX_PLAIN;
+    G.a.fx.out = out;
+    G.a.fx.ld_out = (int)rows;
+    CKB(set_smem_attrs());
+    run_gemm(&g, G, s);
+    CKB(cudaGetLastError());
+    CKB(cudaStreamSynchronize(s));
+    Ctl c;
+    CKB(cudaMemcpy(&c, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    if (c.timeout) return fail(h, TDCFIE_E_TIMEOUT, "a bounded device-side wait ran out (tensor-core pipeline)");
+    return TDCFIE_OK;
 }
 
 }  // namespace tdc

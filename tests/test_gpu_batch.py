@@ -86,3 +86,72 @@ def test_batch_rejects_bad_input():
     with pytest.raises(TdcfieError):
         b.step(1)                        # no excitation
     b.close()
+
+
+# ---------------------------------------------------------------- persistent form
+# every member FP32 with one wave and the direct solve: one cooperative kernel per step
+PCASES = [  # mesh, dt (uneven sizes and lags; a torus; one mesh whose edge count is not a multiple of 4)
+    (meshes.icosphere(2), 0.2),
+    (meshes.torus(1.0, 0.3, 16, 8), 0.3),
+    (meshes.icosphere(1), 0.4),
+    (meshes.ellipsoid(3, (1.8, 0.9, 0.6)), 0.25),
+    (meshes.torus(1.0, 0.4, 10, 5), 0.5),
+    (meshes.icosphere(3), 0.2),
+]
+
+
+def _psolvers(nt):
+    from paper_2312_06367_gb300 import Solver
+    out = []
+    for i, ((V, F), dt) in enumerate(PCASES):
+        s = Solver(V, F, dt=dt, nt=nt, precision="fp32", R=1).assemble()
+        s.set_excitation(_pw(100 + i, 1))
+        out.append(s)
+    return out
+
+
+def test_persistent_batch_equals_individual_marches():
+    import torch
+    from paper_2312_06367_gb300 import Batch
+    nt = 40
+    ss = _psolvers(nt)
+    assert any(s.ne % 4 for s in ss) and len({s.K for s in ss}) > 2
+    b = Batch(ss)
+    cfg = b.tune(2)
+    assert cfg["persistent"] == 1
+    outs = [torch.zeros((nt, 1, s.ne), dtype=torch.float32, device="cuda") for s in ss]
+    b.step(15, [o[:15] for o in outs])
+    b.step(nt - 15, [o[15:] for o in outs])
+    t = b.timing()
+    b.close()
+    torch.cuda.synchronize()
+    assert t["launches"] == 1
+    for i, s in enumerate(ss):
+        ref = torch.zeros_like(outs[i])
+        s.march(_pw(100 + i, 1), ref)
+        torch.cuda.synchronize()
+        assert torch.isfinite(ref).all()
+        assert torch.equal(outs[i], ref), i
+    print(f"persistent batch of {len(ss)}: {t['step_ms']:.3f} ms per step, tuned {cfg}")
+
+
+def test_persistent_batch_member_matches_oracle():
+    import torch
+    from oracle import mot, rhs
+    from oracle.assemble import Operators
+    from oracle.formulation import Formulation
+    from paper_2312_06367_gb300 import Batch
+    nt = 40
+    ss = _psolvers(nt)
+    outs = [torch.zeros((nt, 1, s.ne), dtype=torch.float32, device="cuda") for s in ss]
+    b = Batch(ss)
+    b.step(nt, outs)
+    b.close()
+    torch.cuda.synchronize()
+    (V, F), dt = PCASES[1]
+    ops = Operators(V, F, dt=dt)
+    fm = Formulation(ops)
+    e, h = rhs.incident_tests(ops, _pw(101, 1), dt * np.arange(1, nt + 1))
+    j_ref = fm.postprocess(mot.march_factored(fm, fm.rhs(e, h)))
+    j = outs[1].double().cpu().numpy().transpose(0, 2, 1)
+    assert np.linalg.norm(j - j_ref) / np.linalg.norm(j_ref) < 1e-5

@@ -6,8 +6,9 @@ The FP32 path accumulates every row dot product error-free (FMA product errors a
 remaining error is the FP32 storage of blocks and vectors: it must meet the reduced-precision bar,
 rel-L2 <= 1e-5, against the FP64 oracle (480 edges) and against the oracle-verified FP64 GPU path
 (1920 edges, where the oracle assembly takes too long for a test).  The tensor-core FP16X3 path
-accumulates in the tensor cores' FP32 accumulator; its error here is measured and bounded by the
-value recorded with the design notes (it does not meet 1e-5 at this time step)."""
+keeps per-step roundings near FP32 level (three fp16 slices per vector entry, a separate
+accumulator for the leading product, one accumulator per 64-wide k tile, FP64 partial sums and
+FP64 y_n, b_n, u), so it is held to the same bar."""
 import numpy as np
 import pytest
 
@@ -62,8 +63,29 @@ def test_fp32_small_dt_1920_edges_vs_fp64_path():
     assert err < 1e-5
 
 
-def test_fp16x3_small_dt_480_edges_measured(ico2_oracle):
+def test_fp16x3_small_dt_480_edges_vs_oracle(ico2_oracle):
     j = _gpu(2, 400, "fp16x3", 64)[:, :, :4]
     err = rel(j, ico2_oracle)
     print(f"fp16x3, 480 edges, dt 0.05: rel-L2 {err:.2e}")
-    assert np.all(np.isfinite(j)) and err < 1e-4
+    assert np.all(np.isfinite(j)) and err < 1e-5
+
+
+def test_fp16x3_small_dt_1920_edges_vs_fp64_path():
+    """One FP64 assembly; the FP64 path (8 waves) against the FP16X3 path (64 waves) on the same blocks."""
+    import torch
+    from paper_2312_06367_gb300 import Solver
+    V, F = meshes.icosphere(3)
+    nt = 300
+    s = Solver(V, F, dt=DT, nt=nt, precision="fp64", R=8).assemble()
+    pw8 = {k: v[:8] for k, v in PW.items()}
+    ref = torch.zeros((nt, 8, s.ne), dtype=torch.float64, device="cuda")
+    s.march(pw8, ref)
+    s.replan("fp16x3", 64)
+    out = torch.zeros((nt, 64, s.ne), dtype=torch.float32, device="cuda")
+    s.march(PW, out)
+    torch.cuda.synchronize()
+    s.close()
+    a, b = out[:, :8].double().cpu().numpy(), ref.cpu().numpy()
+    err = rel(a, b)
+    print(f"fp16x3, 1920 edges, dt 0.05: rel-L2 vs FP64 path {err:.2e}")
+    assert np.all(np.isfinite(a)) and err < 1e-5

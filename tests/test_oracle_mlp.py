@@ -33,3 +33,15 @@ def test_features_definition():
     assert np.allclose(X.reshape(5, 2, 8)[3, 1, 0], yh[7, 3, 1] / s[1])
     assert np.allclose(X.reshape(5, 2, 8)[3, 1, 7], yh[0, 3, 1] / s[1])
     assert np.allclose(Y.reshape(5, 2)[4, 0], (yh[8, 4, 0] - yh[7, 4, 0]) / s[0])
+
+
+def test_extrapolation_is_exact_for_cubics():
+    """The cubic extrapolation reproduces any cubic in the step index exactly (and its features
+    target is then zero)."""
+    n = np.arange(9.0)
+    cub = (0.3 + 1.1 * n - 0.2 * n ** 2 + 0.05 * n ** 3)[:, None, None] * np.ones((9, 4, 2))
+    assert np.allclose(mlp.extrapolate(cub), cub[-1], rtol=0, atol=1e-12)
+    quart = (n ** 4)[:, None, None] * np.ones((9, 1, 1))
+    assert abs(mlp.extrapolate(quart)[0, 0] - quart[-1, 0, 0]) == 24.0     # 4th difference of n^4
+    _, Y, _ = mlp.features(cub + 1.0, base="extrap")
+    assert np.max(np.abs(Y)) < 1e-12
