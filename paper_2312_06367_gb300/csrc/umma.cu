@@ -49,7 +49,7 @@ namespace tdc {
 constexpr int BM = 128;      // rows per tile (UMMA M)
 constexpr int BK = 64;       // 16-bit elements per 128-byte row of a tile
 constexpr int NR = 64;       // right-hand sides (UMMA N)
-constexpr int STAGES = 3;
+constexpr int STAGES = 4;
 constexpr int NEPI = 16;                    // epilogue warps: 4 TMEM lane quarters x 4 column groups
 constexpr int NTHREADS = 64 + 32 * NEPI;    // producer warp, MMA warp, epilogue warps
 constexpr int EC = NR / (NEPI / 4);         // columns (right-hand sides) per epilogue warp
@@ -68,7 +68,7 @@ struct Cfg {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int X_BYTES = NR * BK * 2;
     static constexpr int STAGE = 2 * A_BYTES + XS * X_BYTES;
-    static constexpr int MISC = 3072;      // barriers, flags, reduction scratch, tile scales
+    static constexpr int MISC = 1536;      // barriers, flags, reduction scratch, tile scales
     static constexpr int SMEM = STAGES * STAGE + 1024 /*align*/ + MISC;
     static_assert(SMEM <= 232448, "shared memory per CTA");
     static constexpr int TMEM_COLS = 512;   // NBUF buffers x (D0 parts, D1)
@@ -79,7 +79,7 @@ enum { FIX_PLAIN = 0, FIX_SPLIT = 1, FIX_SOLVE = 2 };
 // what the CTA that completes a row tile does with the tile's sums s[r][row]
 struct FixOut {
     int mode;
-    double* out;          // PLAIN: out[r * ld_out + row]; SOLVE: out[((n % 2) * NR + r) * ld_out + row]
+    double* out;          // PLAIN: out[r * ld_out + row]; SOLVE: dy_n to out[(NR + r) * ld_out + row], y_n += dy_n
     int ld_out;
     uint16_t* xs[3];      // SPLIT/SOLVE: destination slices, each [slots][NR][ld_x]
     float* sx;            // inverse scales [slots][ld_x / 64][NR]
@@ -118,14 +118,16 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
 
+// test for the phase; a thread whose phase is open is suspended for up to 20 us (the hint) instead
+// of spinning, so waiting warps leave the issue slots to the working ones
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
+        : "r"(smem_u32(b)), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -291,9 +293,29 @@ __device__ __forceinline__ void split_value(double v, uint16_t* out) {
     }
 }
 
+// (H + L) (a float pair, already scaled) -> XS 16-bit slices: H's leading slice, then the
+// remainder (H - s0) + L (exact subtraction, one rounding of the small remainder)
+template <bool F16, int XS>
+__device__ __forceinline__ void split_pair(float H, float L, uint16_t* out) {
+    const uint16_t b0 = to16<F16>(H);
+    out[0] = b0;
+    float r = (H - from16<F16>(b0)) + L;
+#pragma unroll
+    for (int i = 1; i < XS; ++i) {
+        const uint16_t b = to16<F16>(r);
+        out[i] = b;
+        r -= from16<F16>(b);
+    }
+}
+
 #ifndef TDC_XHI_BITS
 #define TDC_XHI_BITS 11
 #endif
+#ifndef TDC_FP16_XS
+#define TDC_FP16_XS 3
+#endif
+constexpr int FP16_XS = TDC_FP16_XS;   // fp16 slices per vector entry on the FP16X3 path
+
 // Vector slices: the leading slice keeps XHI significant bits (rounded to nearest), the others
 // carry the remainder.  Fewer leading bits shorten the products A_hi x_hi that share the leading
 // accumulator, so fewer of their bits fall below the tensor core's alignment window.
@@ -325,11 +347,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint64_t* empty = full + STAGES;
     uint64_t* acc_full = empty + STAGES;     // [NBUF]
     uint64_t* acc_empty = acc_full + NBUF;   // [NBUF]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + NBUF);
+    uint64_t* sx_full = acc_empty + NBUF;    // [NBUF] the tile scales of a buffer have landed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sx_full + NBUF);
     int* last_flag = reinterpret_cast<int*>(tmem_slot + 1);
     float* red = reinterpret_cast<float*>(misc + 256);    // [NEPI / 4 column groups][4 quads][FIXR] tile maxima
-    float* sx_stage = reinterpret_cast<float*>(misc + 1024);             // [STAGES][NR] x scales of a stage
-    float* sx_buf = reinterpret_cast<float*>(misc + 1024 + STAGES * NR * 4);   // [NBUF][NR] of an accumulator
+    float* sx_buf = reinterpret_cast<float*>(misc + 512);   // [NBUF][NR] x scales of an accumulator's tile
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     const int64_t ipt = (int64_t)g.nblk * g.ktiles;     // iterations per row tile
@@ -340,7 +362,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(full + s, 1); mbar_init(empty + s, 1); }
         // acc_full: the MMA commit and the MMA thread's copy of the tile's x scales
-        for (int b = 0; b < NBUF; ++b) { mbar_init(acc_full + b, 2); mbar_init(acc_empty + b, 32 * NEPI); }
+        for (int b = 0; b < NBUF; ++b) { mbar_init(acc_full + b, 1); mbar_init(acc_empty + b, NEPI); mbar_init(sx_full + b, 1); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -358,17 +380,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             const uint64_t pa = policy_evict_first(), pb = policy_evict_last();
-            int stage = 0;
-            uint32_t phase = 0;
+            int stage = 0, buf = 0;
+            uint32_t phase = 0, ephase = 0;   // ephase bit b: phase parity of accumulator buffer b
+            // (row tile, block, k tile) of the iteration, advanced without divisions
+            int rt = (int)(begin / ipt);
+            int q = (int)((begin - rt * ipt) / g.ktiles);
+            int kt = (int)(begin - rt * ipt - (int64_t)q * g.ktiles);
             for (int64_t it = begin; it < end; ++it) {
-                const int rt = (int)(it / ipt);
-                const int64_t rem = it - rt * ipt;
-                const int q = (int)(rem / g.ktiles), kt = (int)(rem - (int64_t)q * g.ktiles);
                 const int slot = slot_of(g, q, n);
                 if (!mbar_wait(empty + stage, phase ^ 1u, ctl)) break;
+                // the tile's 64 x scales go to its accumulator buffer's slot, free once the epilogue
+                // has released that buffer (the tile NBUF earlier)
+                if (!mbar_wait(acc_empty + buf, ((ephase >> buf) & 1u) ^ 1u, ctl)) break;
+                ephase ^= 1u << buf;
                 uint8_t* st = smem + stage * C::STAGE;
-                mbar_expect_tx(full + stage, C::STAGE + NR * 4);
-                bulk_load(sx_stage + stage * NR, g.sX + ((int64_t)slot * g.ktiles + kt) * NR, NR * 4, full + stage);
+                mbar_expect_tx(sx_full + buf, NR * 4);
+                bulk_load(sx_buf + buf * NR, g.sX + ((int64_t)slot * g.ktiles + kt) * NR, NR * 4, sx_full + buf);
+                mbar_expect_tx(full + stage, C::STAGE);
                 tma_load_3d(st, &tAh, kt * BK, rt * BM, q, full + stage, pa);
                 tma_load_3d(st + C::A_BYTES, &tAl, kt * BK, rt * BM, q, full + stage, pa);
                 uint8_t* xt = st + 2 * C::A_BYTES;
@@ -376,6 +404,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tma_load_3d(xt + C::X_BYTES, &tX1, kt * BK, 0, slot, full + stage, pb);
                 if constexpr (XS == 3) tma_load_3d(xt + 2 * C::X_BYTES, &tX2, kt * BK, 0, slot, full + stage, pb);
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                buf = buf + 1 == NBUF ? 0 : buf + 1;
+                if (++kt == g.ktiles) {
+                    kt = 0;
+                    if (++q == g.nblk) { q = 0; ++rt; }
+                }
             }
         }
     } else if (warp == 1) {
@@ -410,16 +443,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         umma(d1, al + adv, x1 + adv, id, 1);
                     }
                 }
-                {   // the tile's x scales follow its accumulator (the stage is released below)
-                    const float4* src = reinterpret_cast<const float4*>(sx_stage + stage * NR);
-                    float4* dst = reinterpret_cast<float4*>(sx_buf + buf * NR);
-#pragma unroll
-                    for (int c = 0; c < NR / 4; ++c) dst[c] = src[c];
-                }
                 umma_commit(empty + stage);
                 if (++stage == STAGES) { stage = 0; phase ^= 1u; }
                 umma_commit(acc_full + buf);
-                mbar_arrive(acc_full + buf);
                 buf = buf + 1 == NBUF ? 0 : buf + 1;
             }
         }
@@ -434,21 +460,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int c = 0; c < EC; ++c) acc_hi[c] = acc_lo[c] = 0.f;
         int seg = 0, buf = 0;
         bool ok = true;
-        float sa = 1.f;
-        int64_t sa_rt = -1;
+        int64_t rt = begin / ipt, pos = begin - rt * ipt;   // row tile and iteration within it
         for (int64_t it = begin; it < end; ++it) {
-            const int64_t rt = it / ipt;
-            const int64_t rem = it - rt * ipt;
-            const int q = (int)(rem / g.ktiles), kt = (int)(rem - (int64_t)q * g.ktiles);
             if (ok && !mbar_wait(acc_full + buf, (fphase >> buf) & 1u, ctl)) ok = false;
+            if (ok && !mbar_wait(sx_full + buf, (fphase >> buf) & 1u, ctl)) ok = false;
             fphase ^= 1u << buf;
             if (ok) {
                 tc_fence_after();
-                if (rt != sa_rt) {   // one scale per row for all blocks: reload at a new row tile
-                    const int grow = (int)rt * BM + row;
-                    sa = grow < g.rows ? g.sA[grow] : 1.f;
-                    sa_rt = rt;
-                }
                 const float* sx = sx_buf + buf * NR + cbase;
                 const uint32_t d0 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BUFC + cbase);
 #pragma unroll
@@ -461,7 +479,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int c = 0; c < 16; c += 4) {
                         const float4 s4 = *reinterpret_cast<const float4*>(sx + c0 + c);
-                        const float sc[4] = {s4.x * sa, s4.y * sa, s4.z * sa, s4.w * sa};
+                        const float sc[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {   // power-of-two scales: the products are exact
 #pragma unroll
@@ -472,15 +490,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(acc_empty + buf);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty + buf);   // the warp's TMEM reads are complete
             }
             buf = buf + 1 == NBUF ? 0 : buf + 1;
-            if (it + 1 == end || (it + 1) % ipt == 0) {   // end of this CTA's part of row tile rt
+            const bool tile_end = ++pos == ipt;
+            if (it + 1 == end || tile_end) {   // end of this CTA's part of row tile rt
                 float* dst = g.partial + ((int64_t)blockIdx.x * g.maxseg + seg) * (int64_t)2 * NR * BM;
+                // one power-of-two row scale for all blocks: applied once here (exact)
+                const int grow = (int)rt * BM + row;
+                const float sa = grow < g.rows ? g.sA[grow] : 1.f;
 #pragma unroll
                 for (int c = 0; c < EC; ++c) {
-                    dst[(int64_t)(cbase + c) * BM + row] = acc_hi[c];
-                    dst[(int64_t)(NR + cbase + c) * BM + row] = acc_lo[c];
+                    dst[(int64_t)(cbase + c) * BM + row] = acc_hi[c] * sa;
+                    dst[(int64_t)(NR + cbase + c) * BM + row] = acc_lo[c] * sa;
                     acc_hi[c] = acc_lo[c] = 0.f;
                 }
                 ++seg;
@@ -506,26 +529,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const int slot = fx.slot_ring > 0 ? (int)(n % fx.slot_ring) : 0;
                     const int p0 = g.seg_ptr[rt], p1 = g.seg_ptr[rt + 1];
                     for (int r0 = cbase; r0 < cbase + EC; r0 += FIXR) {
-                        double s[FIXR];
+                        float sh[FIXR], sl_[FIXR];
 #pragma unroll
-                        for (int j = 0; j < FIXR; ++j) s[j] = 0.0;
-                        for (int k = p0; k < p1; ++k) {
+                        for (int j = 0; j < FIXR; ++j) sh[j] = sl_[j] = 0.f;
+                        for (int k = p0; k < p1; ++k) {      // the tile's partials in a fixed order
                             const float* P = g.partial + (int64_t)g.seg_slot[k] * 2 * NR * BM;
 #pragma unroll
-                            for (int j = 0; j < FIXR; ++j)
-                                s[j] += (double)__ldcg(P + (int64_t)(r0 + j) * BM + row) +
-                                        (double)__ldcg(P + (int64_t)(NR + r0 + j) * BM + row);
+                            for (int j = 0; j < FIXR; ++j) {
+                                two_sum_acc(sh[j], sl_[j], __ldcg(P + (int64_t)(r0 + j) * BM + row));
+                                sl_[j] += __ldcg(P + (int64_t)(NR + r0 + j) * BM + row);
+                            }
                         }
                         if (fx.mode != FIX_SPLIT && grow < g.rows) {
-                            double* o = fx.out + (fx.mode == FIX_SOLVE ? (n % 2) * (int64_t)NR * fx.ld_out : 0);
-#pragma unroll
-                            for (int j = 0; j < FIXR; ++j) o[(int64_t)(r0 + j) * fx.ld_out + grow] = s[j];
-                        }
-                        if (split) {
-                            // tile maxima over the 64 rows of each half: warps (2 half, 2 half + 1) of this column half
 #pragma unroll
                             for (int j = 0; j < FIXR; ++j) {
-                                float m = fabsf((float)s[j]);
+                                const double v = (double)sh[j] + (double)sl_[j];
+                                if (fx.mode == FIX_SOLVE) {     // increment dy_n, and y_n = y_{n-1} + dy_n
+                                    fx.out[(int64_t)(NR + r0 + j) * fx.ld_out + grow] = v;
+                                    fx.out[(int64_t)(r0 + j) * fx.ld_out + grow] += v;
+                                } else {
+                                    fx.out[(int64_t)(r0 + j) * fx.ld_out + grow] = v;
+                                }
+                            }
+                        }
+                        if (split) {
+                            // tile maxima over the 64 rows of each half: warps (2 half, 2 half + 1) of this column group
+#pragma unroll
+                            for (int j = 0; j < FIXR; ++j) {
+                                float m = fabsf(sh[j] + sl_[j]);
                                 if (!(m == m)) m = INFINITY;
                                 for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
                                 if (lane == 0) red[(ch * 4 + quad) * FIXR + j] = m;
@@ -537,7 +568,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                     const float mx = fmaxf(red[(ch * 4 + 2 * half) * FIXR + j], red[(ch * 4 + 2 * half + 1) * FIXR + j]);
                                     const float sc = fill_scale(mx);
                                     uint16_t sl[3];
-                                    split_vector<F16, XS>(s[j] * (double)sc, sl);
+                                    split_pair<F16, XS>(sh[j] * sc, sl_[j] * sc, sl);
                                     const int64_t off = ((int64_t)slot * NR + r0 + j) * fx.ld_x + grow;
 #pragma unroll
                                     for (int i = 0; i < XS; ++i) fx.xs[i][off] = sl[i];
@@ -550,6 +581,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
             }
+            if (tile_end) { ++rt; pos = 0; }
         }
     }
     tc_fence_before();
@@ -636,12 +668,22 @@ __global__ void __launch_bounds__(256) k_split_x(const double* __restrict__ x, i
 }
 
 // ---------------------------------------------------------------- plane-wave tests, split
-// e_m(t_n) = sum_x c(x).p_r env_r(x, t_n), h_m(t_n) = sum_x c(x).(k_r x p_r) env_r(x, t_n),
-// env_r(x, t) = amp_r exp(-((t - k_r.x - t0_r)/width_r)^2) (Sec. II-C tests of the incident
-// field).  One block per (64-edge tile, 16 waves): compensated FP32 sums over the quadrature
-// points, then the split into the e (slot ring) and h (slot ring + 1) slices of the history
-// operand with one scale per (slot, tile, wave).  t - t0 is carried as an FP32 pair so that late
-// times lose no digits of the pulse's argument.
+// The tensor-core step marches the increments dy_n = y_n - y_{n-1} (y_i = 0 for i <= 0): subtracting
+// the MOT recurrence at step n - 1 from that at step n (Sec. IV-B) gives
+//     sum_{k >= 0} T_k dy_{n-k} = r_n - r_{n-1},      r_0 = 0,
+// the same recurrence for the increments, and the post-processing (Eq. post_processing) uses dy_n
+// itself: j_n = P^LH y_n + P^S dy_n / dtt, y_n = y_{n-1} + dy_n in FP64.  The per-step rounding of
+// the split arithmetic then scales with |dy_n| instead of |y_n|; the time difference of y, which
+// is what the post-processing magnifies, is never formed by subtraction.
+//
+// Increments of the plane-wave tests (Sec. II-C): e_m(t_n) - e_m(t_{n-1}) = sum_x c(x).p
+// [env_r(x, t_n) - env_r(x, t_{n-1})] with env_r(x, t) = amp_r exp(-a^2), a = (t - k_r.x - t0_r) /
+// width_r, and the difference written as -amp_r exp(-a_n^2) expm1(d (2 a_n - d)), d = dt / width_r,
+// so that it keeps its relative precision; at n = 1 the test itself (r_0 = 0).  Same for h.  One
+// block per (64-edge tile, 16 waves): compensated FP32 sums over the quadrature points, then the
+// split into the e (slot ring) and h (slot ring + 1) slices of the history operand with one scale
+// per (slot, tile, wave).  t - t0 is carried as an FP32 pair so that late times lose no digits of
+// the pulse's argument.
 constexpr int RHS_RB = 16;
 template <bool F16, int XS>
 __global__ void __launch_bounds__(256) k_rhs_tc(int ne, const double* __restrict__ exc, double dt, const Ctl* ctl,
@@ -658,8 +700,11 @@ __global__ void __launch_bounds__(256) k_rhs_tc(int ne, const double* __restrict
     const double* P = exc + 11 * r;
     const float kx = (float)P[0], ky = (float)P[1], kz = (float)P[2], qx = (float)P[3], qy = (float)P[4], qz = (float)P[5];
     const float amp = (float)P[6], inv_w = (float)(1.0 / P[8]);
-    const double tt = (double)ctl->n * dt - P[7];
+    const int64_t n = ctl->n;
+    const double tt = (double)n * dt - P[7];
     const float tt_hi = (float)tt, tt_lo = (float)(tt - (double)tt_hi);
+    const float d = (float)(dt / P[8]);
+    const bool first = n == 1;
     const float hx = ky * qz - kz * qy, hy = kz * qx - kx * qz, hz = kx * qy - ky * qx;   // k x p
     float me = 0.f, mh = 0.f;
     for (int i = 0; i < 4; ++i) {
@@ -671,7 +716,8 @@ __global__ void __launch_bounds__(256) k_rhs_tc(int ne, const double* __restrict
             for (int qp = b; qp < end; ++qp) {
                 const float x = px[3 * qp], y = px[3 * qp + 1], z = px[3 * qp + 2];
                 const float arg = ((tt_hi - fmaf(kx, x, fmaf(ky, y, kz * z))) + tt_lo) * inv_w;
-                const float env = amp * expf(-arg * arg);
+                float env = amp * expf(-arg * arg);
+                if (!first) env = -env * expm1f(d * (2.f * arg - d));     // env(t_n) - env(t_{n-1})
                 const float cx = pc[3 * qp], cy = pc[3 * qp + 1], cz = pc[3 * qp + 2];
                 if (qp < me_) two_sum_acc(e_hi, e_lo, env * fmaf(cx, qx, fmaf(cy, qy, cz * qz)));
                 else two_sum_acc(h_hi, h_lo, env * fmaf(cx, hx, fmaf(cy, hy, cz * hz)));
@@ -709,8 +755,8 @@ __global__ void __launch_bounds__(256) k_rhs_tc(int ne, const double* __restrict
 }
 
 // ---------------------------------------------------------------- projector in / out
-// z[r][c] = sum_j tsign[c][j] w[r][tedge[c][j]], w = (1/dtt - 1) y_n - y_{n-1}/dtt, from the FP64
-// pair of the last two y; split into the z slices with one scale per (64-triangle tile, wave).
+// z[r][c] = sum_j tsign[c][j] w[r][tedge[c][j]], w = dy_n / dtt - y_n (= (1/dtt - 1) y_n - y_{n-1}/dtt)
+// from the FP64 y_n and dy_n; split into the z slices with one scale per (64-triangle tile, wave).
 template <bool F16, int XS>
 __global__ void __launch_bounds__(256) k_project_in_tc(DevMesh m, const Ctl* ctl, const double* __restrict__ y2,
                                                        double dtt, uint16_t* __restrict__ Z0, uint16_t* __restrict__ Z1,
@@ -719,9 +765,9 @@ __global__ void __launch_bounds__(256) k_project_in_tc(DevMesh m, const Ctl* ctl
     __shared__ float scl[RHS_RB];
     const int tile = blockIdx.x, rb = blockIdx.y * RHS_RB;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int64_t n = ctl->n;
-    const double* yn = y2 + (n % 2) * (int64_t)NR * m.ne;
-    const double* yp = y2 + ((n + 1) % 2) * (int64_t)NR * m.ne;
+    (void)ctl;
+    const double* yn = y2;                          // y_n
+    const double* dy = y2 + (int64_t)NR * m.ne;     // dy_n
     float mx = 0.f;
     // thread -> (wave rb + (t >> 4) ... ): 16 waves x 64 triangles, 4 per thread, triangles fastest
     for (int i = t; i < RHS_RB * 64; i += 256) {
@@ -730,7 +776,7 @@ __global__ void __launch_bounds__(256) k_project_in_tc(DevMesh m, const Ctl* ctl
         if (c < m.nc) {
             for (int k = 0; k < 3; ++k) {
                 const int e = m.tedge[3 * c + k];
-                const double w = (1.0 / dtt - 1.0) * yn[(int64_t)r * m.ne + e] - yp[(int64_t)r * m.ne + e] / dtt;
+                const double w = dy[(int64_t)r * m.ne + e] / dtt - yn[(int64_t)r * m.ne + e];
                 s += m.tsign[3 * c + k] * w;
             }
         }
@@ -768,7 +814,7 @@ __global__ void k_project_out_tc(DevMesh m, int R, Ctl* ctl, const double* __res
     const int64_t n = ctl->n;
     if (idx < m.ne * R) {
         const int r = idx / m.ne, e = idx % m.ne;
-        const double yv = y2[((n % 2) * R + r) * (int64_t)m.ne + e];
+        const double yv = y2[(int64_t)r * m.ne + e];
         const double val = yv + u[(int64_t)r * m.nc + m.cplus_[e]] - u[(int64_t)r * m.nc + m.cminus_[e]];
         if (!isfinite(val) && atomicCAS(&ctl->status, 0, (int)TDCFIE_E_NONFINITE) == 0) ctl->bad_step = n;
         if (ctl->out) reinterpret_cast<float*>(ctl->out)[((n - ctl->n0) * R + r) * (int64_t)m.ne + e] = (float)val;
@@ -837,7 +883,7 @@ struct TcStep {
     uint16_t* Z[3] = {nullptr, nullptr, nullptr};   // z [R][ldc]
     float *sAh = nullptr, *sAs = nullptr, *sAp = nullptr;   // inverse row scales
     float *sXh = nullptr, *sXb = nullptr, *sXz = nullptr;   // inverse tile scales of the vectors
-    double *y2 = nullptr, *u = nullptr;             // FP64 y_n / y_{n-1} pair [2][R][ne], u [R][nc]
+    double *y2 = nullptr, *u = nullptr;             // FP64 y_n and dy_n [2][R][ne], u [R][nc]
     int* done = nullptr;
     float* partial = nullptr;
     Gemm hist, solve, proj;
@@ -982,7 +1028,7 @@ tdcfie_status build_tc(tdcfie_t h, StepPlan* p) {
     auto* g = new TcStep();
     p->gemm = g;
     g->fp16 = (p->prec == TDCFIE_FP16X3);
-    g->xs = g->fp16 ? 3 : 2;
+    g->xs = g->fp16 ? FP16_XS : 2;
     const int XS = g->xs;
     cudaStream_t s = h->stream;
     int dev = 0;
@@ -1058,7 +1104,7 @@ tdcfie_status build_tc(tdcfie_t h, StepPlan* p) {
         G->a.idesc = id;
         G->a.fx = FixOut{};
     }
-    // history: b_n -> slices of the solve's vector operand
+    // history: d_n -> slices of the solve's vector operand
     g->hist.a.slot_mode = 0;
     g->hist.a.sA = g->sAh;
     g->hist.a.sX = g->sXh;
@@ -1066,7 +1112,7 @@ tdcfie_status build_tc(tdcfie_t h, StepPlan* p) {
     g->hist.a.fx.ld_x = ld;
     g->hist.a.fx.sx = g->sXb;
     for (int i = 0; i < 3; ++i) g->hist.a.fx.xs[i] = g->B[i];
-    // solve: y_n -> FP64 pair (post-processing) and the history ring slot n mod (K - 1)
+    // solve: dy_n -> FP64 dy_n, y_n += dy_n (post-processing) and the history ring slot n mod (K - 1)
     g->solve.a.sA = g->sAs;
     g->solve.a.sX = g->sXb;
     g->solve.a.fx.mode = FIX_SOLVE;
@@ -1093,22 +1139,22 @@ void launch_step_tc(tdcfie_t h, StepPlan* p, cudaStream_t s) {
     TcStep* g = p->gemm;
     const int R = p->R, ne = p->ne, ring = p->ring, ld = g->ld, ldc = g->ldc;
     const dim3 grhs(ld / 64, R / RHS_RB), gproj(ldc / 64, R / RHS_RB);
-    // 1. plane-wave tests -> e, h slots of the history operand
+    // 1. increments of the plane-wave tests -> e, h slots of the history operand
     if (g->fp16)
-        k_rhs_tc<true, 3><<<grhs, 256, 0, s>>>(ne, h->dexc, h->dt, p->ctl, p->pptr, (const float*)p->px,
+        k_rhs_tc<true, FP16_XS><<<grhs, 256, 0, s>>>(ne, h->dexc, h->dt, p->ctl, p->pptr, (const float*)p->px,
                                                 (const float*)p->pc, p->pnE, g->X[0], g->X[1], g->X[2], g->sXh, ring, ld);
     else
         k_rhs_tc<false, 2><<<grhs, 256, 0, s>>>(ne, h->dexc, h->dt, p->ctl, p->pptr, (const float*)p->px,
                                                  (const float*)p->pc, p->pnE, g->X[0], g->X[1], g->X[2], g->sXh, ring, ld);
-    // 2. history sum b_n = -A e_n + alpha L2 h_n - sum_k T_k y_{n-k}  (events bracket the GEMM alone)
+    // 2. increment of the history sum d_n = -A de_n + alpha L2 dh_n - sum_k T_k dy_{n-k}  (events bracket the GEMM)
     cudaEventRecordWithFlags(p->evA, s, cudaEventRecordExternal);
     run_gemm(g, g->hist, s);
     cudaEventRecordWithFlags(p->evB, s, cudaEventRecordExternal);
-    // 3. y_n = T_0^-1 b_n  (FP64 pair slot n % 2; slices into history slot n % ring)
+    // 3. dy_n = T_0^-1 d_n, y_n = y_{n-1} + dy_n (FP64); dy_n's slices into history slot n % ring
     run_gemm(g, g->solve, s);
-    // 4. projector: z = Sigma^T w_n, u = (Sigma^T Sigma)^+ z, j_n = y_n + Sigma u
+    // 4. projector: z = Sigma^T w_n, u = (Sigma^T Sigma)^+ z, j_n = y_n + Sigma u = P^LH y_n + P^S dy_n / dtt
     if (g->fp16)
-        k_project_in_tc<true, 3><<<gproj, 256, 0, s>>>(h->dm, p->ctl, g->y2, h->dtt, g->Z[0], g->Z[1], g->Z[2], g->sXz, ldc);
+        k_project_in_tc<true, FP16_XS><<<gproj, 256, 0, s>>>(h->dm, p->ctl, g->y2, h->dtt, g->Z[0], g->Z[1], g->Z[2], g->sXz, ldc);
     else
         k_project_in_tc<false, 2><<<gproj, 256, 0, s>>>(h->dm, p->ctl, g->y2, h->dtt, g->Z[0], g->Z[1], g->Z[2], g->sXz, ldc);
     run_gemm(g, g->proj, s);
@@ -1129,7 +1175,7 @@ tdcfie_status tc_gemm(int precision, const double* blocks, int64_t nblk, int64_t
         return fail(h, TDCFIE_E_ARG, "sizes out of range (1 <= nblk <= 4096, 1 <= rows, cols <= 2^20)");
     if (!encoder()) return fail(h, TDCFIE_E_CUDA, "cuTensorMapEncodeTiled entry point not available");
     const bool f16 = precision == TDCFIE_FP16X3;
-    const int XS = f16 ? 3 : 2;
+    const int XS = f16 ? FP16_XS : 2;
     const int ld = round_up((int)cols, BK);
     int dev = 0, sms = 0;
     CKB(cudaGetDevice(&dev));
@@ -1162,7 +1208,7 @@ tdcfie_status tc_gemm(int precision, const double* blocks, int64_t nblk, int64_t
         CKB(split_blocks(f16, s, sb, (int)rows, (int)cols, ld, rowmax, g.sAh));
     }
     const dim3 gx(ld / 64, (unsigned)nblk);
-    if (f16) k_split_x<true, 3><<<gx, 256, 0, s>>>(x, (int)cols, ld, g.X[0], g.X[1], g.X[2], g.sXh);
+    if (f16) k_split_x<true, FP16_XS><<<gx, 256, 0, s>>>(x, (int)cols, ld, g.X[0], g.X[1], g.X[2], g.sXh);
     else k_split_x<false, 2><<<gx, 256, 0, s>>>(x, (int)cols, ld, g.X[0], g.X[1], g.X[2], g.sXh);
     CKB(cudaGetLastError());
     bool ok = make_map(&G.ah, g.Ah, cols, rows, nblk, ld, BM, f16) && make_map(&G.al, g.Al, cols, rows, nblk, ld, BM, f16);
