@@ -50,9 +50,16 @@ constexpr int BM = 128;      // rows per tile (UMMA M)
 constexpr int BK = 64;       // 16-bit elements per 128-byte row of a tile
 constexpr int NR = 64;       // right-hand sides (UMMA N)
 constexpr int STAGES = 4;
-constexpr int NEPI = 16;                    // epilogue warps: 4 TMEM lane quarters x 4 column groups
+#ifndef TDC_NEPI
+#define TDC_NEPI 8
+#endif
+constexpr int NEPI = TDC_NEPI;              // epilogue warps: 4 TMEM lane quarters x NEPI / 4 column groups
 constexpr int NTHREADS = 64 + 32 * NEPI;    // producer warp, MMA warp, epilogue warps
 constexpr int EC = NR / (NEPI / 4);         // columns (right-hand sides) per epilogue warp
+#ifndef TDC_LDC
+#define TDC_LDC 16
+#endif
+constexpr int LDC = TDC_LDC < EC ? TDC_LDC : EC;   // TMEM columns per tcgen05.ld of the epilogue
 constexpr int FIXR = 4;      // right-hand sides per pass of the row-tile reduction
 #ifndef TDC_D0S
 #define TDC_D0S 1
@@ -247,10 +254,29 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
         : "r"(taddr));
 }
+template <int W>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* v) {
+    if constexpr (W == 32) tmem_ld32(taddr, v);
+    else tmem_ld16(taddr, v);
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // named barrier of the epilogue warps
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory"); }
+
+// TwoSum on packed pairs (two FP32 lanes per instruction, sm_100+): hi + lo += v with the rounding
+// error of each addition carried into lo.  x - y is written fma(y, -1, x): one rounding, exact
+// like the subtraction.
+__device__ __forceinline__ void two_sum_acc2(float2& hi, float2& lo, float2 v) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 t = __fadd2_rn(hi, v);
+    const float2 bp = __ffma2_rn(hi, m1, t);   // t - hi
+    const float2 a = __ffma2_rn(bp, m1, t);    // t - bp
+    const float2 e1 = __ffma2_rn(a, m1, hi);   // hi - (t - bp)
+    const float2 e2 = __ffma2_rn(bp, m1, v);   // v - bp
+    lo = __fadd2_rn(lo, __fadd2_rn(e1, e2));
+    hi = t;
+}
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
     const float t = hi + v;
@@ -455,9 +481,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int quad = warp & 3, ch = (warp - 2) >> 2;
         const int row = quad * 32 + lane, cbase = ch * EC;
         uint32_t fphase = 0;   // bit b: phase parity of accumulator buffer b
-        float acc_hi[EC], acc_lo[EC];
+        float2 acc_hi[EC / 2], acc_lo[EC / 2];   // columns (2c, 2c + 1) packed
 #pragma unroll
-        for (int c = 0; c < EC; ++c) acc_hi[c] = acc_lo[c] = 0.f;
+        for (int c = 0; c < EC / 2; ++c) acc_hi[c] = acc_lo[c] = make_float2(0.f, 0.f);
         int seg = 0, buf = 0;
         bool ok = true;
         int64_t rt = begin / ipt, pos = begin - rt * ipt;   // row tile and iteration within it
@@ -470,22 +496,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const float* sx = sx_buf + buf * NR + cbase;
                 const uint32_t d0 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BUFC + cbase);
 #pragma unroll
-                for (int c0 = 0; c0 < EC; c0 += 16) {
-                    uint32_t v0[D0S][16], v1[16];
+                for (int c0 = 0; c0 < EC; c0 += LDC) {
+                    uint32_t v0[D0S][LDC], v1[LDC];
 #pragma unroll
-                    for (int part = 0; part < D0S; ++part) tmem_ld16(d0 + part * NR + c0, v0[part]);
-                    tmem_ld16(d0 + D0S * NR + c0, v1);
+                    for (int part = 0; part < D0S; ++part) tmem_ld<LDC>(d0 + part * NR + c0, v0[part]);
+                    tmem_ld<LDC>(d0 + D0S * NR + c0, v1);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int c = 0; c < 16; c += 4) {
+                    for (int c = 0; c < LDC; c += 4) {
                         const float4 s4 = *reinterpret_cast<const float4*>(sx + c0 + c);
-                        const float sc[4] = {s4.x, s4.y, s4.z, s4.w};
+                        const float2 sc[2] = {make_float2(s4.x, s4.y), make_float2(s4.z, s4.w)};
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {   // power-of-two scales: the products are exact
+                        for (int u = 0; u < 4; u += 2) {   // power-of-two scales: the products are exact
+                            const int k = (c0 + c + u) >> 1;
 #pragma unroll
                             for (int part = 0; part < D0S; ++part)
-                                two_sum_acc(acc_hi[c0 + c + u], acc_lo[c0 + c + u], __uint_as_float(v0[part][c + u]) * sc[u]);
-                            acc_lo[c0 + c + u] += __uint_as_float(v1[c + u]) * sc[u];
+                                two_sum_acc2(acc_hi[k], acc_lo[k],
+                                             __fmul2_rn(make_float2(__uint_as_float(v0[part][c + u]),
+                                                                    __uint_as_float(v0[part][c + u + 1])), sc[u >> 1]));
+                            acc_lo[k] = __ffma2_rn(make_float2(__uint_as_float(v1[c + u]), __uint_as_float(v1[c + u + 1])),
+                                                   sc[u >> 1], acc_lo[k]);
                         }
                     }
                 }
@@ -501,10 +531,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int grow = (int)rt * BM + row;
                 const float sa = grow < g.rows ? g.sA[grow] : 1.f;
 #pragma unroll
-                for (int c = 0; c < EC; ++c) {
-                    dst[(int64_t)(cbase + c) * BM + row] = acc_hi[c] * sa;
-                    dst[(int64_t)(NR + cbase + c) * BM + row] = acc_lo[c] * sa;
-                    acc_hi[c] = acc_lo[c] = 0.f;
+                for (int c = 0; c < EC / 2; ++c) {
+                    dst[(int64_t)(cbase + 2 * c) * BM + row] = acc_hi[c].x * sa;
+                    dst[(int64_t)(cbase + 2 * c + 1) * BM + row] = acc_hi[c].y * sa;
+                    dst[(int64_t)(NR + cbase + 2 * c) * BM + row] = acc_lo[c].x * sa;
+                    dst[(int64_t)(NR + cbase + 2 * c + 1) * BM + row] = acc_lo[c].y * sa;
+                    acc_hi[c] = acc_lo[c] = make_float2(0.f, 0.f);
                 }
                 ++seg;
                 __threadfence();
