@@ -28,7 +28,7 @@ L2_BYTES = 126 * 2 ** 20
 METRIC = "MOT steps/s"
 
 
-def workload(name: str, precision: str | None = None):
+def workload(name: str, precision: str | None = None, waves: int | None = None, form: str = "dense"):
     from synth import workloads
     w = {
         "sphere480_fp64": workloads.sphere480_fp64,
@@ -39,6 +39,12 @@ def workload(name: str, precision: str | None = None):
     }[name]()
     if precision:
         w["precision"] = precision
+    if waves:
+        w["pw"] = {k: v[:waves] for k, v in w["pw"].items()}
+        w["name"] = f"{w['name']}_waves{waves}"
+    w["form"] = form
+    if form != "dense":
+        w["name"] = f"{w['name']}_{form}"
     if name == "torus864_fp32":
         # alpha = 1 puts a real polynomial eigenvalue of modulus 1.89 outside the unit circle at
         # this time step on this torus; alpha = 0.5 keeps the spectrum inside (radius 0.84)
@@ -121,6 +127,14 @@ def whole_job_rate(dev_ms: float, steps: int, ws: int, pg=None, device="cpu"):
     return ws * steps / (tot_ms / 1e3), tot_ms
 
 
+def oracle_threads() -> int:
+    """Threads the oracle's BLAS may use: the thread-count variable when one is set, else every core."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k, "").isdigit():
+            return int(os.environ[k])
+    return os.cpu_count()
+
+
 def cpu_oracle_dense_rate(w, steps: int = 3):
     """Oracle dense march (oracle.mot.march_dense, FP64 numpy) on blocks of the workload's size.
 
@@ -182,7 +196,7 @@ def run_reference(args, w):
     if rank != 0:
         return 0
     rate, n, t_asm = cpu_oracle_rate(w, args.steps * 20, budget_s=min(60.0, 5.0 * args.steps))
-    cores = os.cpu_count()
+    cores = oracle_threads()
     sample = (f"{n} march steps after an untimed {t_asm:.1f} s assembly" if t_asm is not None else
               f"oracle dense march, {n} steps on dense FP64 blocks of the workload's size (synthetic values; "
               f"the FP64 oracle assembly of this mesh is out of reach), rate in full-history steps")
@@ -456,7 +470,8 @@ def accuracy_in_run(s, w, nt, stream):
         s.replan(p, r)
         out = torch.zeros((nt, r, s.ne), dtype=s.dtype, device="cuda")
         with torch.cuda.stream(stream):
-            s.march(pw, out)
+            s.set_excitation(pw)
+            s.step(nt, out)
         torch.cuda.synchronize()
         return out.double().cpu().numpy()
 
@@ -468,6 +483,55 @@ def accuracy_in_run(s, w, nt, stream):
            "rel_l2_vs_fp64_path": rel(got, ref), "plain_fp32_rel_l2_vs_fp64_path": rel(one, ref[:, :1]),
            "bar": 1e-5}
     res["meets_bar"] = res["rel_l2_vs_fp64_path"] <= 1e-5
+    return res
+
+
+def factored_study(s, w, steps, warmup, nt_acc, stream):
+    """The two forms of the history sum on the workload's mesh with one incident wave, same FP64
+    assembly: the dense T_k stream (k_history + k_reduce) against the shell-sparse factored form
+    (k_shells, then one dense product with T_0^-1 [-A | alpha L2 | -L1 Sigma]); per path precision
+    the step rate, the history kernels' time and algorithmic bytes, the matrix bytes per step, and
+    the rel-L2 of the factored currents against the dense ones over nt_acc steps."""
+    import numpy as np
+    import torch
+    one = {k: v[:1] for k, v in w["pw"].items()}
+    pk = peaks()
+    res = {}
+    for prec in ("fp32", "fp64"):
+        s.replan(prec, 1)                  # keeps the handle's history form: measure that one first
+        first = s.history_stats()["form"]
+        row = {}
+        cur = {}
+        for form in (first, "factored" if first == "dense" else "dense"):
+            if form != first:
+                s.set_history_form(form)
+            st = s.history_stats()
+            acc = torch.zeros((nt_acc, 1, s.ne), dtype=s.dtype, device="cuda")
+            with torch.cuda.stream(stream):
+                s.set_excitation(one)
+                s.step(nt_acc, acc)
+                s.set_excitation(one)
+                s.step(warmup)
+                s.step(steps)
+            torch.cuda.synchronize()
+            t = s.timing()
+            cur[form] = acc.double().cpu().numpy()
+            h_ms = t["history_ms"]
+            gbs = st["history_bytes"] / (h_ms / 1e3) / 1e9 if h_ms > 0 else None
+            row[form] = {"steps_s": 1e3 / t["step_ms"], "step_ms": t["step_ms"], "history_ms": h_ms,
+                         "history_bytes": st["history_bytes"], "step_bytes": st["step_bytes"],
+                         "history_gbs": gbs, "history_frac_hbm": gbs / pk["hbm_gbs"] if gbs else None,
+                         "launches_per_step": t["launches"] // max(1, steps)}
+            if form == "factored":
+                row[form]["shell_nnz"] = st["nnz"]
+                row[form]["shell_nnz_per_ne2"] = st["nnz"] / s.ne ** 2
+        d, f = cur["dense"], cur["factored"]
+        row["rel_l2_factored_vs_dense"] = float(np.linalg.norm(f - d) / np.linalg.norm(d))
+        row["speedup"] = row["factored"]["steps_s"] / row["dense"]["steps_s"]
+        row["step_bytes_ratio"] = row["factored"]["step_bytes"] / row["dense"]["step_bytes"]
+        res[prec] = row
+    res["R"] = 1
+    res["accuracy_steps"] = nt_acc
     return res
 
 
@@ -497,6 +561,9 @@ def run_ours(args, w):
                R=R if not tensor else 8, stream=stream.cuda_stream, device=local).assemble()
     if prec != "fp64" or tensor:
         s.replan(prec, R)
+    factored = w.get("form", "dense") == "factored"
+    if factored:
+        s.set_history_form("factored")
     t_asm = time.time() - t0
     esz = 8 if prec == "fp64" else 4
     work_bytes = s.timing()["history_bytes"]
@@ -563,7 +630,8 @@ def run_ours(args, w):
         "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16x3": "bf16x3", "fp16x3": "fp16x3"}[prec],
         "data": "synthetic",
         "config": {"workload": w["name"], "edges": s.ne, "triangles": s.nc, "R": R, "K": s.K, "dt": w["dt"],
-                   "alpha": w["alpha"], "precision": prec,
+                   "alpha": w["alpha"], "precision": prec, "history_form": s.history_stats()["form"],
+                   "step_matrix_bytes": s.history_stats()["step_bytes"],
                    "cache": "L2 flushed between timed steps" if flush else "inputs larger than L2",
                    "assemble_s": round(t_asm, 2), "wall_s": round(wall1 - wall0, 4), "finite": finite},
         "e2e": {"value": e2e, "unit": "steps/s", "h2d_bytes_per_step": 88 * R / args.steps,
@@ -571,7 +639,8 @@ def run_ours(args, w):
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                      "frac": (achieved / pk["hbm_gbs"]) if achieved else None, "traffic": traffic,
-                     "kernel": ("history sum (k_history + k_reduce)" if prec in ("fp64", "fp32") else
+                     "kernel": ("factored history sum over all lags of S_k, MM'_k, Phi_k (k_shells)" if factored else
+                                "history sum (k_history + k_reduce)" if prec in ("fp64", "fp32") else
                                 "tcgen05 split-precision history GEMM (k_tc_gemm, fixup in-kernel)"),
                      "algorithmic_bytes_per_launch": work_bytes, "history_ms": h_ms,
                      "peak_source": "measured" if not pk.get("fallback") else "fallback"},
@@ -595,12 +664,14 @@ def run_ours(args, w):
             "batched_wave_steps_s": value / ws * R, "speedup_per_wave": value / ws * R / plain,
             "rel_l2_batched_vs_fp64": acc["rel_l2_vs_fp64_path"],
             "rel_l2_plain_vs_fp64": acc["plain_fp32_rel_l2_vs_fp64_path"]}
+        if not args.no_factored:
+            line["factored_form"] = factored_study(s, w, 20, 3, min(args.accuracy_steps, 200), stream)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n, t_casm = cpu_oracle_rate(w, 4 * args.steps + 50)
         sample = (f"{n} march steps of the same workload (assembly {t_casm:.1f} s untimed)" if t_casm is not None else
                   f"oracle dense march, {n} steps on dense FP64 blocks of the workload's size (synthetic values; "
                   f"the FP64 oracle assembly of this mesh is out of reach), rate in full-history steps")
-        line["cpu_baseline"] = {"value": rate, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+        line["cpu_baseline"] = {"value": rate, "unit": "steps/s", "cores": oracle_threads(), "kind": "oracle",
                                 "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -618,9 +689,14 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=None, help="override the workload's path precision")
+    ap.add_argument("--waves", type=int, default=None, help="march only the first N incident waves")
+    ap.add_argument("--history-form", default="dense", choices=["dense", "factored"],
+                    help="history sum over the dense T_k or the shell-sparse factored form (FP64/FP32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the in-run accuracy check")
     ap.add_argument("--accuracy-steps", type=int, default=300, help="steps of the in-run accuracy check")
+    ap.add_argument("--no-factored", action="store_true",
+                    help="skip the dense-versus-factored history comparison on the workload's mesh")
     ap.add_argument("--accuracy", action="store_true",
                     help="full-size accuracy of the reduced-precision paths against the FP64 path")
     ap.add_argument("--train-epochs", type=int, default=4, help="learned-guess training passes (ellipsoid12288)")
@@ -637,7 +713,7 @@ def main():
                               "same GPU handles stepped one after another, not against the oracle"}))
             return 0
         return run_batch(args, probs, args.workload)
-    w = workload(args.workload, args.precision)
+    w = workload(args.workload, args.precision, args.waves, args.history_form)
     if args.impl == "reference":
         return run_reference(args, w)
     if args.accuracy:

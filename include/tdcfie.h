@@ -192,6 +192,26 @@ tdcfie_status tdcfie_replan(tdcfie_t h, int precision, int64_t max_rhs);
  * again at the next step.  GMRES statistics keep accumulating until the next set_excitation. */
 tdcfie_status tdcfie_set_solver(tdcfie_t h, int solver, int guess, double gmres_tol);
 
+/* How the history sum of the FP64 and FP32 paths is streamed (Sec. IV-A, Eq. dis_TD_CFIE):
+ *   TDCFIE_HISTORY_DENSE     the dense blocks T_k, k = 1..K-1, multiplied out at assembly (default);
+ *   TDCFIE_HISTORY_FACTORED  the shell-sparse retarded matrices S_k, MM_k (+ G/2 at k = 0) and Phi_k
+ *     (all lags of a row in one compressed row, lag and column packed in 32 bits), applied to rings of
+ *     the physical currents j_i (Eq. post_processing) and the charges Sigma^T y_i, followed per step by
+ *     one dense product with W = T_0^-1 [-A | alpha L2 | -L1 Sigma] (formed once in FP64) and by the
+ *     projector pair with the dual-graph Laplacian pseudo-inverse.  Same recurrence, other association:
+ *     it streams about sum_k nnz(shells) + 3.1 N^2 entries per step instead of (K + 2) N^2.
+ * tdcfie_set_history_form rebuilds the step plan of an assembled handle (the excitation must be set
+ * again); tdcfie_replan keeps the form (the tensor-core paths always stream dense blocks).  FACTORED needs the FP64 or FP32 path, the direct solve, K <= 256, fewer than 2^24 edges and
+ * the FP64 assembly (not released); the FP64 path also needs a handle assembled with precision FP64.
+ * TDCFIE_E_UNSUPPORTED / TDCFIE_E_STATE otherwise, and the handle keeps no plan after a failed rebuild.
+ * tdcfie_history_stats (host outputs, any may be NULL): the form of the current plan, the nonzeros of
+ * the shells (0 for the dense form), the algorithmic bytes per step of the history kernels and of all
+ * matrices the step streams. */
+typedef enum { TDCFIE_HISTORY_DENSE = 0, TDCFIE_HISTORY_FACTORED = 1 } tdcfie_history_form;
+tdcfie_status tdcfie_set_history_form(tdcfie_t h, int form);
+tdcfie_status tdcfie_history_stats(tdcfie_t h, int32_t* form, int64_t* nnz, double* history_bytes,
+                                   double* step_bytes);
+
 /*
  * Several scatterers marched together (the uneven-batch case; the paper marches one scatterer).
  * Every tdcfie_batch_step advances all handles by one launch of a CUDA graph captured at the first
@@ -245,7 +265,8 @@ tdcfie_status tdcfie_bc_table(tdcfie_t h, int64_t* nentries, int32_t* fine_tri, 
 
 /* Copy an assembled FP64 matrix to a host buffer (row-major):
  *   which 0: T_k (ne x ne), 1: S_k (ne x ne), 2: H_k (ne x ne), 3: MM_k (ne x ne),
- *   4: G, 5: Z^s, 6: Z^h, 7: M, 8: P^Sigma, 9: L1, 10: L2 (ne x ne; k ignored). */
+ *   4: G, 5: Z^s, 6: Z^h, 7: M, 8: P^Sigma, 9: L1, 10: L2 (ne x ne; k ignored),
+ *   11: Phi_k (nc x nc, the charge-potential matrix with H_k = Sigma Phi_k Sigma^T). */
 tdcfie_status tdcfie_get_matrix(tdcfie_t h, int which, int64_t k, double* host_out);
 
 /* Device time (ms, CUDA events on the handle's stream) of the last tdcfie_step call and of its

@@ -119,6 +119,7 @@ def mlp_samples(y, base: str = "prev", stream=None):
     return X, Y
 
 
+_FORM = {"dense": 0, "factored": 1}
 _SOLVE = {"direct": _lib.SOLVE_DIRECT, "gmres": _lib.SOLVE_GMRES}
 _GUESS = {"zero": _lib.GUESS_ZERO, "prev": _lib.GUESS_PREV, "mlp": _lib.GUESS_MLP, "extrap": _lib.GUESS_EXTRAP,
           "mlp_extrap": _lib.GUESS_MLP_EXTRAP}
@@ -189,8 +190,10 @@ class Solver:
         return self
 
     def matrix(self, which: str, k: int = 0) -> np.ndarray:
-        ids = {"T": 0, "S": 1, "H": 2, "MM": 3, "G": 4, "Zs": 5, "Zh": 6, "M": 7, "PS": 8, "L1": 9, "L2": 10}
-        out = np.zeros((self.ne, self.ne), dtype=np.float64)
+        ids = {"T": 0, "S": 1, "H": 2, "MM": 3, "G": 4, "Zs": 5, "Zh": 6, "M": 7, "PS": 8, "L1": 9, "L2": 10,
+               "Phi": 11}
+        n = self.nc if which == "Phi" else self.ne
+        out = np.zeros((n, n), dtype=np.float64)
         _lib.check(_lib.load().tdcfie_get_matrix(self._h, ids[which], int(k), _lib._ptr(out)), self._h)
         return out
 
@@ -228,6 +231,20 @@ class Solver:
     def set_solver(self, solver: str = "gmres", guess: str = "prev", gmres_tol: float = 1e-8):
         """Switch the per-step solve of the assembled handle (tdcfie_set_solver)."""
         _lib.check(_lib.load().tdcfie_set_solver(self._h, _SOLVE[solver], _GUESS[guess], float(gmres_tol)), self._h)
+
+    def set_history_form(self, form: str = "factored"):
+        """Stream the dense T_k ("dense") or the shell-sparse retarded matrices ("factored") in the
+        history sum (tdcfie_set_history_form); the excitation must be set again."""
+        _lib.check(_lib.load().tdcfie_set_history_form(self._h, _FORM[form]), self._h)
+
+    def history_stats(self):
+        """Form of the current plan, shell nonzeros and algorithmic bytes per step (tdcfie_history_stats)."""
+        f, n = ctypes.c_int32(), ctypes.c_int64()
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _lib.check(_lib.load().tdcfie_history_stats(self._h, ctypes.byref(f), ctypes.byref(n), ctypes.byref(a),
+                                                    ctypes.byref(b)), self._h)
+        return {"form": ("dense", "factored")[f.value], "nnz": n.value, "history_bytes": a.value,
+                "step_bytes": b.value}
 
     def mlp_load(self, params):
         """Load 4801 learned-guess parameters (array-like, float32) into the march."""

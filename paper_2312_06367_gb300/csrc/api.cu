@@ -271,6 +271,39 @@ extern "C" tdcfie_status tdcfie_set_solver(tdcfie_t h, int solver, int guess, do
     return plan_set_solver(h, solver, guess, gmres_tol);
 }
 
+extern "C" tdcfie_status tdcfie_set_history_form(tdcfie_t h, int form) {
+    if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
+    if (form != TDCFIE_HISTORY_DENSE && form != TDCFIE_HISTORY_FACTORED) return fail(h, TDCFIE_E_ARG, "bad history form");
+    if (!h->assembled || !h->plan) return fail(h, TDCFIE_E_STATE, "call tdcfie_assemble first");
+    if (form == TDCFIE_HISTORY_FACTORED) {
+        if (h->opts.precision != TDCFIE_FP64 && h->opts.precision != TDCFIE_FP32)
+            return fail(h, TDCFIE_E_UNSUPPORTED, "the factored history form runs on the FP64 and FP32 paths");
+        if (h->opts.solver != TDCFIE_SOLVE_DIRECT)
+            return fail(h, TDCFIE_E_UNSUPPORTED, "the factored history form uses the direct solve");
+    }
+    if (h->released) return fail(h, TDCFIE_E_STATE, "the FP64 assembly was released (tdcfie_release_assembly)");
+    const int old = h->history_form;
+    h->history_form = form;
+    h->excited = false;
+    const tdcfie_status st = build_plan(h);
+    if (st != TDCFIE_OK) {
+        h->history_form = old;
+        free_plan(h);
+    }
+    return st;
+}
+
+extern "C" tdcfie_status tdcfie_history_stats(tdcfie_t h, int32_t* form, int64_t* nnz, double* history_bytes,
+                                              double* step_bytes) {
+    if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
+    if (!h->plan) return fail(h, TDCFIE_E_STATE, "call tdcfie_assemble first");
+    if (form) *form = h->plan->fact ? TDCFIE_HISTORY_FACTORED : TDCFIE_HISTORY_DENSE;
+    if (nnz) *nnz = h->plan->fact ? fact_nnz(h->plan, false) : 0;
+    if (history_bytes) *history_bytes = h->hist_bytes;
+    if (step_bytes) *step_bytes = h->step_bytes;
+    return TDCFIE_OK;
+}
+
 extern "C" tdcfie_status tdcfie_march(tdcfie_t h, const tdcfie_plane_waves* exc, void* out, int out_on_host) {
     tdcfie_status st = tdcfie_set_excitation(h, exc);
     if (st != TDCFIE_OK) return st;
@@ -331,7 +364,7 @@ extern "C" tdcfie_status tdcfie_get_matrix(tdcfie_t h, int which, int64_t k, dou
     if (h->released) return fail(h, TDCFIE_E_STATE, "the FP64 assembly was released (tdcfie_release_assembly)");
     const int64_t ne = h->mesh.ne, NN = ne * ne;
     const double* src = nullptr;
-    const bool lagged = which >= 0 && which <= 3;
+    const bool lagged = (which >= 0 && which <= 3) || which == 11;
     if (lagged && (k < 0 || k >= h->K)) return fail(h, TDCFIE_E_ARG, "lag out of range");
     switch (which) {
         case 0: src = h->T + k * NN; break;
@@ -344,6 +377,10 @@ extern "C" tdcfie_status tdcfie_get_matrix(tdcfie_t h, int which, int64_t k, dou
         case 8: src = h->PS; break;
         case 9: src = h->L1; break;
         case 10: src = h->L2; break;
+        case 11:
+            CK(cudaMemcpy(host_out, h->Phi + k * h->mesh.nc * h->mesh.nc, sizeof(double) * h->mesh.nc * h->mesh.nc,
+                          cudaMemcpyDeviceToHost));
+            return TDCFIE_OK;
         case 2: {
             // H_k = Sigma Phi_k Sigma^T, expanded on the host
             const Mesh& M = h->mesh;

@@ -126,6 +126,8 @@ struct tdcfie_s {
     // timing
     double asm_s[6] = {0, 0, 0, 0, 0, 0};   // upload, retarded EFIE, retarded MFIE, static, formation, plan
     double last_step_ms = 0, last_hist_ms = 0, hist_bytes = 0;
+    double step_bytes = 0;          // matrix bytes streamed per step by the whole plan
+    int history_form = 0;           // tdcfie_history_form of the next plan
     int64_t last_launches = 0;
 };
 

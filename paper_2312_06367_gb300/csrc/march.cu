@@ -205,12 +205,21 @@ __global__ void k_advance(Ctl* ctl) { ctl->n += 1; }
 static size_t esize(int prec) { return prec == TDCFIE_FP64 ? 8 : 4; }
 
 template <typename T>
+void launch_rhs(tdcfie_t h, StepPlan& p, cudaStream_t s) {
+    const int tb = 256;
+    k_rhs<T><<<(p.ne * p.R + tb - 1) / tb, tb, 0, s>>>(p.ne, h->dexc, p.R, h->dt, p.ctl, p.pptr, (const T*)p.px,
+                                                        (const T*)p.pc, p.pnE, (T*)p.E, (T*)p.Hv);
+}
+template void launch_rhs<double>(tdcfie_t, StepPlan&, cudaStream_t);
+template void launch_rhs<float>(tdcfie_t, StepPlan&, cudaStream_t);
+
+template <typename T>
 static cudaError_t launch_step(tdcfie_t h, StepPlan& p, cudaStream_t s) {
+    if (p.fact) return launch_step_fact<T>(h, p, s);
     const tdc::DevMesh& m = h->dm;
     const int R = p.R, ne = p.ne;
     const int tb = 256;
-    k_rhs<T><<<(ne * R + tb - 1) / tb, tb, 0, s>>>(ne, h->dexc, R, h->dt, p.ctl, p.pptr, (const T*)p.px,
-                                                    (const T*)p.pc, p.pnE, (T*)p.E, (T*)p.Hv);
+    launch_rhs<T>(h, p, s);
     const int wpb = 8;   // warps per block
     dim3 g((ne + wpb - 1) / wpb, p.nblk);
 #define HIST(RM) k_history<T, RM><<<g, 32 * wpb, 0, s>>>((const T*)p.blocks, p.nblk, ne, R, p.ring, p.ctl, \
@@ -272,6 +281,7 @@ void free_plan(tdcfie_t h) {
     if (p->gemm) destroy_tc(p->gemm);
     if (p->gm) destroy_gmres(p->gm);
     if (p->mlp) destroy_mlp(p->mlp);
+    if (p->fact) destroy_fact(p->fact);
     if (p->t0mat) cudaFree(p->t0mat);
     if (p->guessbuf) cudaFree(p->guessbuf);
     if (p->evA) cudaEventDestroy(p->evA);
@@ -393,6 +403,10 @@ tdcfie_status build_plan(tdcfie_t h) {
     if (tensor) {
         tdcfie_status st = build_tc(h, p);
         if (st != TDCFIE_OK) return st;
+    } else if (h->history_form == TDCFIE_HISTORY_FACTORED) {
+        tdcfie_status st = build_fact(h, p);
+        if (st != TDCFIE_OK) return st;
+        h->step_bytes = fact_step_bytes(p);
     } else {
         CK(cudaMalloc(&p->blocks, es * p->nblk * ne * ne));
         CK(cudaMalloc(&p->t0inv, es * ne * ne));
@@ -421,7 +435,10 @@ tdcfie_status build_plan(tdcfie_t h) {
     CK(cudaEventCreate(&p->ev2));
     CK(cudaEventCreate(&p->evA));
     CK(cudaEventCreate(&p->evB));
-    h->hist_bytes = (double)p->nblk * ne * ne * (p->prec == TDCFIE_FP64 ? 8.0 : 4.0);
+    if (!tensor && !p->fact) {
+        h->hist_bytes = (double)p->nblk * ne * ne * es;
+        h->step_bytes = h->hist_bytes + (double)ne * ne * es + (double)nc * nc * es;
+    }
     if (h->opts.solver == TDCFIE_SOLVE_GMRES) {
         const tdcfie_status st = plan_set_solver(h, h->opts.solver, h->opts.guess, h->opts.gmres_tol);
         if (st != TDCFIE_OK) return st;
@@ -439,6 +456,8 @@ tdcfie_status plan_set_solver(tdcfie_t h, int solver, int guess, double tol) {
     const size_t es = p->esz;
     if (solver == TDCFIE_SOLVE_GMRES && (p->prec == TDCFIE_BF16X3 || p->prec == TDCFIE_FP16X3))
         return fail(h, TDCFIE_E_UNSUPPORTED, "GMRES runs on the FP64 and FP32 paths");
+    if (solver == TDCFIE_SOLVE_GMRES && p->fact)
+        return fail(h, TDCFIE_E_UNSUPPORTED, "the factored history form uses the direct solve");
     const bool learned = guess == TDCFIE_GUESS_MLP || guess == TDCFIE_GUESS_MLP_EXTRAP;
     if (solver == TDCFIE_SOLVE_GMRES && guess == TDCFIE_GUESS_EXTRAP && p->ring < 4)
         return fail(h, TDCFIE_E_UNSUPPORTED, "the extrapolated guess needs K - 1 >= 4 stored steps");
@@ -475,6 +494,10 @@ tdcfie_status plan_reset(tdcfie_t h) {
     if (p->gm) CK(reset_gmres_stats(p->gm));
     CK(cudaMemcpyAsync(p->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(p->ringbuf, 0, p->esz * p->ring * p->R * p->ne, s));
+    if (p->fact) {
+        const tdcfie_status st = reset_fact(h, p);
+        if (st != TDCFIE_OK) return st;
+    }
     if (p->gemm) CK(reset_tc(p->gemm, p->ring, p->ne, s));
     CK(cudaStreamSynchronize(s));
     return TDCFIE_OK;
@@ -538,10 +561,7 @@ tdcfie_status plan_step(tdcfie_t h, int64_t nsteps, void* out, void* yout) {
     if (!p->exec) {
         // capture one step
         CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        cudaError_t ce = cudaSuccess;
-        if (p->prec == TDCFIE_FP64) ce = launch_step<double>(h, *p, s);
-        else if (p->prec == TDCFIE_FP32) ce = launch_step<float>(h, *p, s);
-        else launch_step_tc(h, p, s);
+        const cudaError_t ce = capture_step(h, s);
         const cudaError_t ee = cudaStreamEndCapture(s, &p->graph);
         if (ce != cudaSuccess) {
             if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }

@@ -8,6 +8,7 @@ namespace tdc {
 struct TcStep;
 struct GmresPlan;
 struct MlpState;
+struct FactPlan;
 
 struct StepPlan {
     int prec = TDCFIE_FP64;
@@ -35,6 +36,8 @@ struct StepPlan {
     Ctl* ctl = nullptr;
     // rhs tables: per edge, quadrature points (x) and weighted basis vectors (c), e-points first
     int* pptr = nullptr; int* pnE = nullptr; void* px = nullptr; void* pc = nullptr;
+    // factored history form (factored.cu); blocks and t0inv are then unused
+    FactPlan* fact = nullptr;
     // tensor-core path
     TcStep* gemm = nullptr;
     cudaGraph_t graph = nullptr;
@@ -46,5 +49,16 @@ struct StepPlan {
     int launches_per_step = 0;
 };
 
+// plane-wave tests e_n, h_n of one step into p.E, p.Hv (march.cu)
+template <typename T>
+void launch_rhs(tdcfie_t h, StepPlan& p, cudaStream_t s);
+// factored history form (factored.cu)
+tdcfie_status build_fact(tdcfie_t h, StepPlan* p);
+tdcfie_status reset_fact(tdcfie_t h, StepPlan* p);
+void destroy_fact(FactPlan* f);
+double fact_step_bytes(const StepPlan* p);
+int64_t fact_nnz(const StepPlan* p, bool stored);
+template <typename T>
+cudaError_t launch_step_fact(tdcfie_t h, StepPlan& p, cudaStream_t s);
 
 }  // namespace tdc

@@ -1164,6 +1164,8 @@ tdcfie_status build_tc(tdcfie_t h, StepPlan* p) {
     CKB(cudaStreamSynchronize(s));
     // algorithmic bytes of the history GEMM: every block (hi + lo) once, and its R vectors (XS slices)
     h->hist_bytes = (double)nblk * ne * ne * 4.0 + (double)nblk * R * ne * 2.0 * XS;
+    // and of the whole step: the history, T_0^-1 and the pseudo-inverse (hi + lo each)
+    h->step_bytes = h->hist_bytes + 4.0 * (double)ne * ne + 4.0 * (double)nc * nc;
     return TDCFIE_OK;
 }
 
