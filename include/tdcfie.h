@@ -244,6 +244,17 @@ tdcfie_status tdcfie_batch_tune(tdcfie_batch_t b, int64_t steps_per_candidate, i
 tdcfie_status tdcfie_batch_timing(tdcfie_batch_t b, double* step_ms, int64_t* launches_per_step);
 tdcfie_status tdcfie_batch_destroy(tdcfie_batch_t b);
 
+/* Far field of marched currents at angular frequency w (Sec. V, the large-time-step test compares
+ * the sphere's far field at 3 Hz with the series solution); units c = eta = mu = 1, phasors e^{j w t}:
+ *   J_m(w) = dt sinc^2(w dt / 2) sum_i j_m[i] e^{-j w t_i}   (hat basis of Eq. post_processing, t_i = i dt)
+ *   F(rhat) = -j w / (4 pi) (I - rhat rhat) sum_m J_m(w) int f_m(r) e^{j w rhat.r} dS   (7-point rule)
+ * so that the scattered field is F e^{-j w r} / r.  currents: DEVICE, nt x R x ne as written by
+ * tdcfie_step from the march's first step (path precision: FP64 on the FP64 path, FP32 otherwise);
+ * rhat: HOST ndir x 3 unit vectors (ndir <= 65535); out: HOST ndir x R x 3 x 2 doubles (re, im).
+ * FP64 arithmetic; synchronous on the handle's stream; TDCFIE_E_ARG for bad arguments. */
+tdcfie_status tdcfie_far_field(tdcfie_t h, const void* currents, int64_t nt, double w, const double* rhat,
+                               int64_t ndir, double* out);
+
 /* Whole march: set_excitation, then nt steps into currents_out.  out_on_host != 0: currents_out is a
  * HOST buffer (pinned or pageable) and the device-to-host copy is part of the call. */
 tdcfie_status tdcfie_march(tdcfie_t h, const tdcfie_plane_waves* exc, void* currents_out, int out_on_host);

@@ -246,6 +246,15 @@ class Solver:
         return {"form": ("dense", "factored")[f.value], "nnz": n.value, "history_bytes": a.value,
                 "step_bytes": b.value}
 
+    def far_field(self, currents, w: float, rhat):
+        """Far-field amplitude (ndir, R, 3) complex at angular frequency w of the currents (torch CUDA
+        tensor (nt, R, ne) from step()/march() starting at the first step) (tdcfie_far_field)."""
+        d = np.ascontiguousarray(np.atleast_2d(np.asarray(rhat, dtype=np.float64)))
+        out = np.zeros((d.shape[0], self.R, 3, 2), dtype=np.float64)
+        _lib.check(_lib.load().tdcfie_far_field(self._h, ctypes.c_void_p(currents.data_ptr()), int(currents.shape[0]),
+                                                float(w), _lib._ptr(d), d.shape[0], _lib._ptr(out)), self._h)
+        return out[..., 0] + 1j * out[..., 1]
+
     def mlp_load(self, params):
         """Load 4801 learned-guess parameters (array-like, float32) into the march."""
         a = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())

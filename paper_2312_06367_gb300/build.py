@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtdcfie.so")
-SOURCES = ["mesh.cpp", "assemble.cu", "linalg.cu", "formation.cu", "march.cu", "factored.cu", "umma.cu", "gemv.cu", "gmres.cu", "mlp.cu", "batch.cu", "api.cu"]
+SOURCES = ["mesh.cpp", "assemble.cu", "linalg.cu", "formation.cu", "march.cu", "factored.cu", "farfield.cu", "umma.cu", "gemv.cu", "gmres.cu", "mlp.cu", "batch.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-Xcompiler", "-O2"]
 

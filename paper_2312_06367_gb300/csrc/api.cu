@@ -304,6 +304,20 @@ extern "C" tdcfie_status tdcfie_history_stats(tdcfie_t h, int32_t* form, int64_t
     return TDCFIE_OK;
 }
 
+extern "C" tdcfie_status tdcfie_far_field(tdcfie_t h, const void* currents, int64_t nt, double w, const double* rhat,
+                                          int64_t ndir, double* out) {
+    if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
+    if (!h->assembled || !h->plan) return fail(h, TDCFIE_E_STATE, "call tdcfie_assemble first");
+    if (!currents || !rhat || !out || nt < 1 || ndir < 1 || !(w >= 0.0) || !std::isfinite(w))
+        return fail(h, TDCFIE_E_ARG, "far field: NULL buffer, nt < 1, ndir < 1 or a bad frequency");
+    if (ndir > 65535) return fail(h, TDCFIE_E_ARG, "far field: at most 65535 directions per call");
+    for (int64_t d = 0; d < ndir; ++d) {
+        const double n2 = rhat[3 * d] * rhat[3 * d] + rhat[3 * d + 1] * rhat[3 * d + 1] + rhat[3 * d + 2] * rhat[3 * d + 2];
+        if (!(std::fabs(n2 - 1.0) < 1e-9)) return fail(h, TDCFIE_E_ARG, "far field: directions must be unit vectors");
+    }
+    return far_field(h, currents, nt, w, rhat, ndir, out);
+}
+
 extern "C" tdcfie_status tdcfie_march(tdcfie_t h, const tdcfie_plane_waves* exc, void* out, int out_on_host) {
     tdcfie_status st = tdcfie_set_excitation(h, exc);
     if (st != TDCFIE_OK) return st;

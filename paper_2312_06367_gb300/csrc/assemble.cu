@@ -37,18 +37,25 @@ __constant__ double c_ax[NANG], c_aw[NANG], c_rx[NRAD], c_rw[NRAD];
 __constant__ double c_r7[7][4];   // barycentric a, b, c, weight
 __constant__ double c_r3[3][4];
 
+void triangle_rule7(double r7[7][4]) {
+    const double s15 = std::sqrt(15.0);
+    const double a1 = (9.0 - 2.0 * s15) / 21.0, b1 = (6.0 + s15) / 21.0, w1 = (155.0 + s15) / 1200.0;
+    const double a2 = (9.0 + 2.0 * s15) / 21.0, b2 = (6.0 - s15) / 21.0, w2 = (155.0 - s15) / 1200.0;
+    const double t[7][4] = {{1.0 / 3, 1.0 / 3, 1.0 / 3, 9.0 / 40.0},
+                            {a1, b1, b1, w1}, {b1, a1, b1, w1}, {b1, b1, a1, w1},
+                            {a2, b2, b2, w2}, {b2, a2, b2, w2}, {b2, b2, a2, w2}};
+    for (int q = 0; q < 7; ++q)
+        for (int c = 0; c < 4; ++c) r7[q][c] = t[q][c];
+}
+
 void set_rule_tables(const RuleTables& r, cudaStream_t s) {
     cudaMemcpyToSymbolAsync(c_ax, r.ax, sizeof(r.ax), 0, cudaMemcpyHostToDevice, s);
     cudaMemcpyToSymbolAsync(c_aw, r.aw, sizeof(r.aw), 0, cudaMemcpyHostToDevice, s);
     cudaMemcpyToSymbolAsync(c_rx, r.rx, sizeof(r.rx), 0, cudaMemcpyHostToDevice, s);
     cudaMemcpyToSymbolAsync(c_rw, r.rw, sizeof(r.rw), 0, cudaMemcpyHostToDevice, s);
     // symmetric rules: degree 5 (7 points) and degree 2 (3 points)
-    const double s15 = std::sqrt(15.0);
-    const double a1 = (9.0 - 2.0 * s15) / 21.0, b1 = (6.0 + s15) / 21.0, w1 = (155.0 + s15) / 1200.0;
-    const double a2 = (9.0 + 2.0 * s15) / 21.0, b2 = (6.0 - s15) / 21.0, w2 = (155.0 - s15) / 1200.0;
-    double r7[7][4] = {{1.0 / 3, 1.0 / 3, 1.0 / 3, 9.0 / 40.0},
-                       {a1, b1, b1, w1}, {b1, a1, b1, w1}, {b1, b1, a1, w1},
-                       {a2, b2, b2, w2}, {b2, a2, b2, w2}, {b2, b2, a2, w2}};
+    double r7[7][4];
+    triangle_rule7(r7);
     double r3[3][4] = {{2.0 / 3, 1.0 / 6, 1.0 / 6, 1.0 / 3}, {1.0 / 6, 2.0 / 3, 1.0 / 6, 1.0 / 3},
                        {1.0 / 6, 1.0 / 6, 2.0 / 3, 1.0 / 3}};
     cudaMemcpyToSymbolAsync(c_r7, r7, sizeof(r7), 0, cudaMemcpyHostToDevice, s);

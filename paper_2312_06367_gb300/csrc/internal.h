@@ -58,6 +58,8 @@ struct DevMesh {
 };
 
 void set_rule_tables(const RuleTables& r, cudaStream_t s);
+// symmetric degree-5 rule on a triangle: per point barycentric (a, b, c) and weight (sum 1)
+void triangle_rule7(double r7[7][4]);
 void launch_retarded_efie(const DevMesh& m, double dt, int K, double T0, double D, double* S, double* Phi,
                           cudaStream_t s);
 void launch_retarded_mfie(const DevMesh& m, double dt, int K, double D, double* MM, cudaStream_t s);
@@ -144,4 +146,6 @@ cudaError_t capture_step(tdcfie_t h, cudaStream_t s);
 tdcfie_status plan_set_outputs(tdcfie_t h, void* out, void* yout);
 tdcfie_status plan_check(tdcfie_t h);
 int plan_launches_per_step(tdcfie_t h);
+tdcfie_status far_field(tdcfie_t h, const void* currents, int64_t nt, double w, const double* rhat, int64_t ndir,
+                        double* out);
 }  // namespace tdc

@@ -712,19 +712,22 @@ __global__ void __launch_bounds__(256) k_split_x(const double* __restrict__ x, i
 // [env_r(x, t_n) - env_r(x, t_{n-1})] with env_r(x, t) = amp_r exp(-a^2), a = (t - k_r.x - t0_r) /
 // width_r, and the difference written as -amp_r exp(-a_n^2) expm1(d (2 a_n - d)), d = dt / width_r,
 // so that it keeps its relative precision; at n = 1 the test itself (r_0 = 0).  Same for h.  One
-// block per (64-edge tile, 16 waves): compensated FP32 sums over the quadrature points, then the
-// split into the e (slot ring) and h (slot ring + 1) slices of the history operand with one scale
-// per (slot, tile, wave).  t - t0 is carried as an FP32 pair so that late times lose no digits of
+// block per (64-edge tile, 16 waves), one thread per (edge, wave): compensated FP32 sums over the
+// quadrature points, then the split into the e (slot ring) and h (slot ring + 1) slices of the
+// history operand with one scale per (slot, tile, wave).  t - t0 is carried as an FP32 pair so that late times lose no digits of
 // the pulse's argument.
 constexpr int RHS_RB = 16;
+constexpr int RHS_NT = 1024;                  // one (edge, wave) pair per thread: 32 warps x 2 edges x 16 waves
+constexpr int RHS_NW = RHS_NT / 32;
+constexpr int RHS_PASS = 64 / (2 * RHS_NW);
 template <bool F16, int XS>
-__global__ void __launch_bounds__(256) k_rhs_tc(int ne, const double* __restrict__ exc, double dt, const Ctl* ctl,
+__global__ void __launch_bounds__(RHS_NT) k_rhs_tc(int ne, const double* __restrict__ exc, double dt, const Ctl* ctl,
                                                 const int* __restrict__ pptr, const float* __restrict__ px,
                                                 const float* __restrict__ pc, const int* __restrict__ nE,
                                                 uint16_t* __restrict__ X0, uint16_t* __restrict__ X1,
                                                 uint16_t* __restrict__ X2, float* __restrict__ sX, int ring, int ld) {
     __shared__ double ev[2][64][RHS_RB + 1];
-    __shared__ float mred[2][8][RHS_RB];
+    __shared__ float mred[2][RHS_NW][RHS_RB];
     __shared__ float scl[2][RHS_RB];
     const int tile = blockIdx.x, rb = blockIdx.y * RHS_RB;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -739,8 +742,8 @@ __global__ void __launch_bounds__(256) k_rhs_tc(int ne, const double* __restrict
     const bool first = n == 1;
     const float hx = ky * qz - kz * qy, hy = kz * qx - kx * qz, hz = kx * qy - ky * qx;   // k x p
     float me = 0.f, mh = 0.f;
-    for (int i = 0; i < 4; ++i) {
-        const int el = 2 * warp + (lane >> 4) + 16 * i;     // edge within the tile
+    for (int i = 0; i < RHS_PASS; ++i) {
+        const int el = 2 * warp + (lane >> 4) + 2 * RHS_NW * i;     // edge within the tile
         const int mm = tile * 64 + el;
         float e_hi = 0.f, e_lo = 0.f, h_hi = 0.f, h_lo = 0.f;
         if (mm < ne) {
@@ -769,14 +772,14 @@ __global__ void __launch_bounds__(256) k_rhs_tc(int ne, const double* __restrict
     if (t < 2 * RHS_RB) {
         const int w = t / RHS_RB, j = t % RHS_RB;
         float m = 0.f;
-        for (int k = 0; k < 8; ++k) m = fmaxf(m, mred[w][k][j]);
+        for (int k = 0; k < RHS_NW; ++k) m = fmaxf(m, mred[w][k][j]);
         if (!(m == m)) m = INFINITY;
         scl[w][j] = fill_scale(m);
         sX[((int64_t)(ring + w) * (ld / 64) + tile) * NR + rb + j] = 1.f / scl[w][j];
     }
     __syncthreads();
     uint16_t* dst[3] = {X0, X1, X2};
-    for (int i = t; i < 2 * RHS_RB * 64; i += 256) {
+    for (int i = t; i < 2 * RHS_RB * 64; i += RHS_NT) {
         const int w = i / (RHS_RB * 64), j = (i / 64) % RHS_RB, el = i & 63;
         uint16_t sl[3];
         split_vector<F16, XS>(ev[w][el][j] * (double)scl[w][j], sl);
@@ -1175,10 +1178,10 @@ void launch_step_tc(tdcfie_t h, StepPlan* p, cudaStream_t s) {
     const dim3 grhs(ld / 64, R / RHS_RB), gproj(ldc / 64, R / RHS_RB);
     // 1. increments of the plane-wave tests -> e, h slots of the history operand
     if (g->fp16)
-        k_rhs_tc<true, FP16_XS><<<grhs, 256, 0, s>>>(ne, h->dexc, h->dt, p->ctl, p->pptr, (const float*)p->px,
+        k_rhs_tc<true, FP16_XS><<<grhs, RHS_NT, 0, s>>>(ne, h->dexc, h->dt, p->ctl, p->pptr, (const float*)p->px,
                                                 (const float*)p->pc, p->pnE, g->X[0], g->X[1], g->X[2], g->sXh, ring, ld);
     else
-        k_rhs_tc<false, 2><<<grhs, 256, 0, s>>>(ne, h->dexc, h->dt, p->ctl, p->pptr, (const float*)p->px,
+        k_rhs_tc<false, 2><<<grhs, RHS_NT, 0, s>>>(ne, h->dexc, h->dt, p->ctl, p->pptr, (const float*)p->px,
                                                  (const float*)p->pc, p->pnE, g->X[0], g->X[1], g->X[2], g->sXh, ring, ld);
     // 2. increment of the history sum d_n = -A de_n + alpha L2 dh_n - sum_k T_k dy_{n-k}  (events bracket the GEMM)
     cudaEventRecordWithFlags(p->evA, s, cudaEventRecordExternal);

@@ -1,0 +1,124 @@
+"""Large-time-step regime and far field on the GPU (Sec. V: the sphere marched with c dt / D ~ 5e4,
+its far field at 3 Hz compared with the series solution).
+
+* FP64 march at dt = 1e5 (the paper's 0.333 ms; pulse w = 8e6 m, t0 = 80 ms, in metres of light
+  travel) against the oracle's factored march: rel-L2 <= 1e-10 on the currents.
+* tdcfie_far_field on the GPU currents against the oracle's far-field evaluation of the same
+  currents: rel <= 1e-12.
+* FP32 path at the same time step: currents within 1e-5 of the FP64 path (its far field is
+  printed, not asserted: the star part of j that carries the electric dipole is 6e-8 of the loop
+  part at this frequency, below FP32 storage).
+* The far field at 3 Hz against the Rayleigh limit of the PEC sphere (equal to the series to
+  O((ka)^2), ka = 6.3e-8): within 5 % on 320 triangles and 1.5 % on 1280 (the polyhedral sphere's
+  error, second order in the mesh size; the oracle measures 3.5 % and 0.9 %).
+"""
+import numpy as np
+import pytest
+
+from synth import excitation, meshes
+
+pytestmark = pytest.mark.gpu
+
+DT = 1e5
+NT = 360
+K3HZ = 2.0 * np.pi * 3.0 / 299792458.0
+
+
+def _dirs():
+    out = []
+    for phi in (0.0, np.pi / 4, np.pi / 2):
+        for t in np.linspace(0.1, np.pi - 0.1, 9):
+            out.append([np.sin(t) * np.cos(phi), np.sin(t) * np.sin(phi), np.cos(t)])
+    return np.array(out)
+
+
+def _pw():
+    return excitation.single(t0=2.4e7, sigma=2e6)
+
+
+def _gpu(level, precision="fp64"):
+    import torch
+    from paper_2312_06367_gb300 import Solver
+    V, F = meshes.icosphere(level)
+    s = Solver(V, F, dt=DT, nt=NT, precision=precision).assemble()
+    out = torch.zeros((NT, 1, s.ne), dtype=s.dtype, device="cuda")
+    s.march(_pw(), out)
+    torch.cuda.synchronize()
+    return s, out
+
+
+def _rayleigh(d):
+    from oracle import farfield
+    pw = _pw()
+    return farfield.rayleigh_sphere(d, K3HZ, 1.0, farfield.incident_amplitude(pw, 0, K3HZ), pw["k"][0])
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def ico2_fp64():
+    return _gpu(2)
+
+
+def test_large_dt_fp64_march_matches_oracle(ico2_fp64):
+    from oracle import mot, rhs
+    from oracle.assemble import Operators
+    from oracle.formulation import Formulation
+    s, out = ico2_fp64
+    assert s.K == 3
+    V, F = meshes.icosphere(2)
+    ops = Operators(V, F, dt=DT)
+    fm = Formulation(ops)
+    e, h = rhs.incident_tests(ops, _pw(), DT * np.arange(1, NT + 1))
+    j_ref = fm.postprocess(mot.march_factored(fm, fm.rhs(e, h)))
+    j = out.double().cpu().numpy().transpose(0, 2, 1)
+    err = rel(j, j_ref)
+    print(f"dt 1e5 (c dt / D = 5e4), 480 edges, FP64: rel-L2 vs oracle {err:.2e}")
+    assert err < 1e-10
+
+
+def test_far_field_kernel_matches_oracle(ico2_fp64):
+    from oracle import farfield
+    from oracle.topology import Topology
+    s, out = ico2_fp64
+    d = _dirs()
+    got = s.far_field(out, K3HZ, d)[:, 0, :]
+    V, F = meshes.icosphere(2)
+    j = out.double().cpu().numpy().transpose(0, 2, 1)
+    want = farfield.far_field(Topology(V, F), j, DT, K3HZ, d)[:, 0, :]
+    err = rel(got, want)
+    print(f"far field, GPU kernel vs oracle evaluation of the same currents: {err:.2e}")
+    assert err < 1e-12
+    # a second frequency and the k = 0 limit of the radiation vector
+    got2 = s.far_field(out, 10 * K3HZ, d)[:, 0, :]
+    want2 = farfield.far_field(Topology(V, F), j, DT, 10 * K3HZ, d)[:, 0, :]
+    assert rel(got2, want2) < 1e-12
+
+
+def test_far_field_at_3hz_vs_rayleigh_converges(ico2_fp64):
+    s2, out2 = ico2_fp64
+    d = _dirs()
+    e2 = rel(s2.far_field(out2, K3HZ, d)[:, 0, :], _rayleigh(d))
+    s3, out3 = _gpu(3)
+    e3 = rel(s3.far_field(out3, K3HZ, d)[:, 0, :], _rayleigh(d))
+    print(f"3 Hz far field vs Rayleigh after the dt = 1e5 march: 320 triangles {e2:.3e}, 1280 triangles {e3:.3e}")
+    assert e2 < 0.05
+    assert e3 < 0.015
+    assert e3 < 0.5 * e2
+
+
+def test_far_field_fp32_path_large_dt(ico2_fp64):
+    s64, out64 = ico2_fp64
+    s32, out32 = _gpu(2, "fp32")
+    d = _dirs()
+    f64 = s64.far_field(out64, K3HZ, d)[:, 0, :]
+    f32 = s32.far_field(out32, K3HZ, d)[:, 0, :]
+    j64 = out64.double().cpu().numpy()
+    j32 = out32.double().cpu().numpy()
+    print(f"FP32 path at dt 1e5: currents rel-L2 vs FP64 path {rel(j32, j64):.2e}, far field {rel(f32, f64):.2e}, "
+          f"vs Rayleigh {rel(f32, _rayleigh(d)):.3e}")
+    assert rel(j32, j64) < 1e-5
+    # not asserted: at k a = 6.3e-8 the electric-dipole part of the far field comes from the star
+    # part of j, about k a = 6e-8 of the loop part, below the FP32 storage of j
