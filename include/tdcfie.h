@@ -244,6 +244,18 @@ tdcfie_status tdcfie_batch_tune(tdcfie_batch_t b, int64_t steps_per_candidate, i
 tdcfie_status tdcfie_batch_timing(tdcfie_batch_t b, double* step_ms, int64_t* launches_per_step);
 tdcfie_status tdcfie_batch_destroy(tdcfie_batch_t b);
 
+/* The system the step marches.  TDCFIE_FORMULATION_QHP_CFIE (default): the qHP TD-CFIE of
+ * Eq. qHP_TDCFIE.  TDCFIE_FORMULATION_MFIE: the mixed TD-MFIE, one of the paper's comparison
+ * formulations (Sec. V), (G/2 + MM) j = h with the hat basis in time and Dirac testing on the same
+ * matrices: sum_k MM'_k j_{n-k} = h_n, MM'_k = MM_k + G/2 [k = 0]; the currents are j directly.
+ * tdcfie_set_formulation rebuilds the plan of an assembled handle (excitation to be set again);
+ * MFIE needs the dense FP64 or FP32 path with the direct solve and the FP64 assembly (not
+ * released): TDCFIE_E_UNSUPPORTED / TDCFIE_E_STATE otherwise; the formulation is kept by
+ * tdcfie_replan, which then refuses the tensor-core paths, as set_history_form and set_solver
+ * refuse the factored form and GMRES. */
+typedef enum { TDCFIE_FORMULATION_QHP_CFIE = 0, TDCFIE_FORMULATION_MFIE = 1 } tdcfie_formulation;
+tdcfie_status tdcfie_set_formulation(tdcfie_t h, int formulation);
+
 /* Far field of marched currents at angular frequency w (Sec. V, the large-time-step test compares
  * the sphere's far field at 3 Hz with the series solution); units c = eta = mu = 1, phasors e^{j w t}:
  *   J_m(w) = dt sinc^2(w dt / 2) sum_i j_m[i] e^{-j w t_i}   (hat basis of Eq. post_processing, t_i = i dt)

@@ -10,7 +10,8 @@ Modules: topology (edges, Lambda, Sigma), bc (barycentric refinement, BC functio
 quad.c/cquad (FP64 quadrature), assemble (retarded and static matrices), formulation
 (projectors, T_k, r_n, post-processing), mot (marching and brute-force block solve),
 rhs (incident-field tests), mlp (learned-guess network), farfield (far field of marched
-currents and the Rayleigh limit of the PEC sphere).  The Mie series of the transient physics
+currents and the Rayleigh limit of the PEC sphere), comparators (the standard TD-EFIE and
+mixed TD-MFIE of the paper's comparisons).  The Mie series of the transient physics
 check lives with the tests (tests/mie_series.py).
 Parity-unpinned parts are listed in the module headers that contain them.
 """

@@ -246,6 +246,11 @@ class Solver:
         return {"form": ("dense", "factored")[f.value], "nnz": n.value, "history_bytes": a.value,
                 "step_bytes": b.value}
 
+    def set_formulation(self, formulation: str = "mfie"):
+        """March the qHP TD-CFIE ("qhp") or the mixed TD-MFIE comparison formulation ("mfie") on the
+        same matrices (tdcfie_set_formulation); the excitation must be set again."""
+        _lib.check(_lib.load().tdcfie_set_formulation(self._h, {"qhp": 0, "mfie": 1}[formulation]), self._h)
+
     def far_field(self, currents, w: float, rhat):
         """Far-field amplitude (ndir, R, 3) complex at angular frequency w of the currents (torch CUDA
         tensor (nt, R, ne) from step()/march() starting at the first step) (tdcfie_far_field)."""

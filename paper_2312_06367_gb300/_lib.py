@@ -68,6 +68,7 @@ SIGNATURES = [
     ("tdcfie_replan", _I, [_P, _I, _I64]),
     ("tdcfie_set_history_form", _I, [_P, _I]),
     ("tdcfie_far_field", _I, [_P, _P, _I64, _D, _P, _I64, _P]),
+    ("tdcfie_set_formulation", _I, [_P, _I]),
     ("tdcfie_history_stats", _I, [_P, _P, _P, _P, _P]),
     ("tdcfie_batch_create", _I, [_P, _I64, _P]),
     ("tdcfie_batch_step", _I, [_P, _I64, _P]),

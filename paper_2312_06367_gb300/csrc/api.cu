@@ -247,6 +247,8 @@ extern "C" tdcfie_status tdcfie_replan(tdcfie_t h, int precision, int64_t max_rh
     if (precision == TDCFIE_FP64 && !h->formed_fp64)
         return fail(h, TDCFIE_E_UNSUPPORTED, "the FP64 path needs blocks formed in FP64 (assemble with precision FP64)");
     if (h->released) return fail(h, TDCFIE_E_STATE, "the FP64 assembly was released (tdcfie_release_assembly)");
+    if (tensor && h->formulation != TDCFIE_FORMULATION_QHP_CFIE)
+        return fail(h, TDCFIE_E_UNSUPPORTED, "the comparison formulation runs on the dense FP64 and FP32 paths");
     if (tensor && h->opts.solver == TDCFIE_SOLVE_GMRES) h->opts.solver = TDCFIE_SOLVE_DIRECT;
     h->opts.precision = precision;
     h->opts.max_rhs = max_rhs;
@@ -280,6 +282,8 @@ extern "C" tdcfie_status tdcfie_set_history_form(tdcfie_t h, int form) {
             return fail(h, TDCFIE_E_UNSUPPORTED, "the factored history form runs on the FP64 and FP32 paths");
         if (h->opts.solver != TDCFIE_SOLVE_DIRECT)
             return fail(h, TDCFIE_E_UNSUPPORTED, "the factored history form uses the direct solve");
+        if (h->formulation != TDCFIE_FORMULATION_QHP_CFIE)
+            return fail(h, TDCFIE_E_UNSUPPORTED, "the comparison formulation runs on the dense FP64 and FP32 paths");
     }
     if (h->released) return fail(h, TDCFIE_E_STATE, "the FP64 assembly was released (tdcfie_release_assembly)");
     const int old = h->history_form;
@@ -288,6 +292,31 @@ extern "C" tdcfie_status tdcfie_set_history_form(tdcfie_t h, int form) {
     const tdcfie_status st = build_plan(h);
     if (st != TDCFIE_OK) {
         h->history_form = old;
+        free_plan(h);
+    }
+    return st;
+}
+
+extern "C" tdcfie_status tdcfie_set_formulation(tdcfie_t h, int formulation) {
+    if (!h) return fail(nullptr, TDCFIE_E_ARG, "handle is NULL");
+    if (formulation != TDCFIE_FORMULATION_QHP_CFIE && formulation != TDCFIE_FORMULATION_MFIE)
+        return fail(h, TDCFIE_E_ARG, "bad formulation");
+    if (!h->assembled || !h->plan) return fail(h, TDCFIE_E_STATE, "call tdcfie_assemble first");
+    if (formulation != TDCFIE_FORMULATION_QHP_CFIE) {
+        if (h->opts.precision != TDCFIE_FP64 && h->opts.precision != TDCFIE_FP32)
+            return fail(h, TDCFIE_E_UNSUPPORTED, "the comparison formulation runs on the dense FP64 and FP32 paths");
+        if (h->opts.solver != TDCFIE_SOLVE_DIRECT)
+            return fail(h, TDCFIE_E_UNSUPPORTED, "the comparison formulation uses the direct solve");
+        if (h->history_form != TDCFIE_HISTORY_DENSE)
+            return fail(h, TDCFIE_E_UNSUPPORTED, "the comparison formulation runs on the dense FP64 and FP32 paths");
+    }
+    if (h->released) return fail(h, TDCFIE_E_STATE, "the FP64 assembly was released (tdcfie_release_assembly)");
+    const int old = h->formulation;
+    h->formulation = formulation;
+    h->excited = false;
+    const tdcfie_status st = build_plan(h);
+    if (st != TDCFIE_OK) {
+        h->formulation = old;
         free_plan(h);
     }
     return st;

@@ -130,6 +130,7 @@ struct tdcfie_s {
     double last_step_ms = 0, last_hist_ms = 0, hist_bytes = 0;
     double step_bytes = 0;          // matrix bytes streamed per step by the whole plan
     int history_form = 0;           // tdcfie_history_form of the next plan
+    int formulation = 0;            // tdcfie_formulation of the next plan
     int64_t last_launches = 0;
 };
 

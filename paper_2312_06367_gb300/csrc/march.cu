@@ -313,6 +313,8 @@ tdcfie_status build_plan(tdcfie_t h) {
     p->esz = esize(p->prec);
     const int64_t ne = M.ne, nc = M.nc, R = p->R;
     const bool tensor = p->prec == TDCFIE_BF16X3 || p->prec == TDCFIE_FP16X3;
+    if (h->formulation != TDCFIE_FORMULATION_QHP_CFIE && (tensor || h->history_form != TDCFIE_HISTORY_DENSE))
+        return fail(h, TDCFIE_E_UNSUPPORTED, "the comparison formulation runs on the dense FP64 and FP32 paths");
     if (tensor) p->esz = 4;   // the tensor-core paths keep FP32 vectors, 16-bit hi/lo matrices
     const size_t es = p->esz;
     // rhs quadrature tables (host, FP64), uploaded in the path precision
@@ -403,6 +405,33 @@ tdcfie_status build_plan(tdcfie_t h) {
     if (tensor) {
         tdcfie_status st = build_tc(h, p);
         if (st != TDCFIE_OK) return st;
+    } else if (h->formulation == TDCFIE_FORMULATION_MFIE) {
+        // mixed TD-MFIE (a comparison formulation of Sec. V): sum_k MM'_k j_{n-k} = h_n with
+        // MM'_0 = MM_0 + G/2; block 0 (e) zero, block 1 (h) the identity, block 1+k: -MM_k; the
+        // unknown is j itself, so the projector product is zero and the post-processing returns y
+        CK(cudaMalloc(&p->blocks, es * p->nblk * ne * ne));
+        CK(cudaMalloc(&p->t0inv, es * ne * ne));
+        CK(cudaMalloc(&p->pinv, es * nc * nc));
+        CK(cudaMemsetAsync(p->blocks, 0, es * ne * ne, s));
+        CK(cudaMemsetAsync(p->pinv, 0, es * nc * nc, s));
+        double *tmp = nullptr, *work = nullptr;
+        CK(cudaMalloc(&tmp, 8 * ne * ne));
+        CK(cudaMalloc(&work, 8 * (2 * ne + 2)));
+        fill_identity(s, tmp, (int)ne, 1.0);
+        to_path(s, p->prec, tmp, (char*)p->blocks + es * ne * ne, ne * ne);
+        for (int k = 1; k < h->K; ++k) {
+            CK(cudaMemcpyAsync(tmp, h->MM + (int64_t)k * ne * ne, 8 * ne * ne, cudaMemcpyDeviceToDevice, s));
+            axpby(s, ne * ne, 0.0, tmp, -1.0, tmp);
+            to_path(s, p->prec, tmp, (char*)p->blocks + es * (1 + k) * ne * ne, ne * ne);
+        }
+        CK(cudaMemcpyAsync(tmp, h->MM, 8 * ne * ne, cudaMemcpyDeviceToDevice, s));
+        axpby(s, ne * ne, 0.5, h->G, 1.0, tmp);
+        const int singular = invert(s, tmp, (int)ne, work);
+        to_path(s, p->prec, tmp, p->t0inv, ne * ne);
+        CK(cudaStreamSynchronize(s));
+        cudaFree(tmp);
+        cudaFree(work);
+        if (singular) return fail(h, TDCFIE_E_STATE, "G/2 + MM_0 is singular");
     } else if (h->history_form == TDCFIE_HISTORY_FACTORED) {
         tdcfie_status st = build_fact(h, p);
         if (st != TDCFIE_OK) return st;
@@ -458,6 +487,8 @@ tdcfie_status plan_set_solver(tdcfie_t h, int solver, int guess, double tol) {
         return fail(h, TDCFIE_E_UNSUPPORTED, "GMRES runs on the FP64 and FP32 paths");
     if (solver == TDCFIE_SOLVE_GMRES && p->fact)
         return fail(h, TDCFIE_E_UNSUPPORTED, "the factored history form uses the direct solve");
+    if (solver == TDCFIE_SOLVE_GMRES && h->formulation != TDCFIE_FORMULATION_QHP_CFIE)
+        return fail(h, TDCFIE_E_UNSUPPORTED, "the comparison formulation uses the direct solve");
     const bool learned = guess == TDCFIE_GUESS_MLP || guess == TDCFIE_GUESS_MLP_EXTRAP;
     if (solver == TDCFIE_SOLVE_GMRES && guess == TDCFIE_GUESS_EXTRAP && p->ring < 4)
         return fail(h, TDCFIE_E_UNSUPPORTED, "the extrapolated guess needs K - 1 >= 4 stored steps");
