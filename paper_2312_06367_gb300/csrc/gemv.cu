@@ -2,6 +2,7 @@
 //   out[r][i] = sum_{q < nblk} sum_{j < n} blocks[q][i][j] x[q][r][j]
 // One warp per (row i, block q) writes the per-block partial sums; a second kernel adds the
 // blocks in a fixed order (deterministic result).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -107,20 +108,28 @@ static __device__ __align__(256) unsigned char g_block_gemv_scratch[NOALLOC_SCRA
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
 static void* g_scratch_addr[NOALLOC_MAX_DEVICES];
+static CUcontext g_scratch_ctx[NOALLOC_MAX_DEVICES];
 static std::mutex g_scratch_mu;
 
-// device address of the scratch array on the current device (looked up once per device)
+// device address of the scratch array on the current device, looked up once per device and
+// context (a cudaDeviceReset gives the device a new primary context and the array a new address)
 static cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    // no allocation and no synchronising call here: cudaGetDevice and cuCtxGetCurrent only, and
+    // the symbol lookup (which also makes the primary context current) when the context is new
+    CUcontext ctx = nullptr;
+    if (cuCtxGetCurrent(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_block_gemv_scratch);
         if (e != cudaSuccess) return e;
+        if (cuCtxGetCurrent(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;
