@@ -712,12 +712,14 @@ __global__ void __launch_bounds__(256) k_split_x(const double* __restrict__ x, i
 // [env_r(x, t_n) - env_r(x, t_{n-1})] with env_r(x, t) = amp_r exp(-a^2), a = (t - k_r.x - t0_r) /
 // width_r, and the difference written as -amp_r exp(-a_n^2) expm1(d (2 a_n - d)), d = dt / width_r,
 // so that it keeps its relative precision; at n = 1 the test itself (r_0 = 0).  Same for h.  One
-// block per (64-edge tile, 16 waves), one thread per (edge, wave): compensated FP32 sums over the
-// quadrature points, then the split into the e (slot ring) and h (slot ring + 1) slices of the
-// history operand with one scale per (slot, tile, wave).  t - t0 is carried as an FP32 pair so that late times lose no digits of
+// block per (64-edge tile, 16 waves): compensated FP32 sums over the quadrature points, then the
+// split into the e (slot ring) and h (slot ring + 1) slices of the history operand with one scale
+// per (slot, tile, wave).  t - t0 is carried as an FP32 pair so that late times lose no digits of
 // the pulse's argument.
 constexpr int RHS_RB = 16;
-constexpr int RHS_NT = 1024;                  // one (edge, wave) pair per thread: 32 warps x 2 edges x 16 waves
+// 8 warps x 2 edges x 16 waves per pass, 4 passes, so that the 480 blocks of the 7680-edge case are
+// resident at once (1024 threads with one pair each fit one block per SM and measured no faster)
+constexpr int RHS_NT = 256;
 constexpr int RHS_NW = RHS_NT / 32;
 constexpr int RHS_PASS = 64 / (2 * RHS_NW);
 template <bool F16, int XS>
