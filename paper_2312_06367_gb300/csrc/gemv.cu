@@ -111,6 +111,21 @@ static void* g_scratch_addr[NOALLOC_MAX_DEVICES];
 static CUcontext g_scratch_ctx[NOALLOC_MAX_DEVICES];
 static std::mutex g_scratch_mu;
 
+// cuCtxGetCurrent through the runtime's driver entry point, so that the library keeps no link-time
+// dependency on the driver library (it loads on hosts without a GPU)
+typedef CUresult (*CtxGetCurrent)(CUcontext*);
+static CtxGetCurrent ctx_get_current() {
+    static CtxGetCurrent fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrent)p;
+    }
+    return fn;
+}
+
 // device address of the scratch array on the current device, looked up once per device and
 // context (a cudaDeviceReset gives the device a new primary context and the array a new address)
 static cudaError_t scratch_address(void** out) {
@@ -120,14 +135,16 @@ static cudaError_t scratch_address(void** out) {
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
     // no allocation and no synchronising call here: cudaGetDevice and cuCtxGetCurrent only, and
     // the symbol lookup (which also makes the primary context current) when the context is new
+    const CtxGetCurrent get = ctx_get_current();
+    if (!get) return cudaErrorDeviceUninitialized;
     CUcontext ctx = nullptr;
-    if (cuCtxGetCurrent(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    if (get(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_block_gemv_scratch);
         if (e != cudaSuccess) return e;
-        if (cuCtxGetCurrent(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+        if (get(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
         g_scratch_addr[dev] = p;
         g_scratch_ctx[dev] = ctx;
     }
