@@ -218,9 +218,9 @@ tdcfie_status tdcfie_history_stats(tdcfie_t h, int32_t* form, int64_t* nnz, doub
  * step, and each handle computes exactly what tdcfie_step computes on it (bit for bit).
  *   Persistent form, used when every handle is FP32 with one incident wave and the direct solve:
  *   the graph holds ONE cooperative kernel that walks a work list of all handles' items
- *   (plane-wave tests, history rows over all blocks, T_0^-1 rows, projector gathers,
- *   pseudo-inverse rows, post-processing), longest items first, with a bounded grid-wide barrier
- *   between the six phases.
+ *   (plane-wave tests, per-block history partial sums of 8 rows x 4 blocks, their reduction in
+ *   block order, T_0^-1 rows, projector gathers, pseudo-inverse rows, post-processing), longest
+ *   items first, with a bounded grid-wide barrier between the seven phases.
  *   Graph-branch form, for any other mix: one step of every handle on its own stream branch.
  *
  * tdcfie_batch_create: handles (host array of n assembled handles on one device, each at most once)

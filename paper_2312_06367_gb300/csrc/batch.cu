@@ -2,9 +2,10 @@
 //
 //  * Persistent (every member FP32, one incident wave, direct solve: the uneven-batch workload):
 //    ONE cooperative kernel per step walks a work list of all members' items -- plane-wave tests
-//    (32 edges), history rows (all K + 1 blocks of CH rows), T_0^-1 rows, projector gathers (32
-//    triangles), pseudo-inverse rows, post-processing (32 edges) -- with grid-wide barriers
-//    between the six phases.  Warps take items from a per-phase counter; the items are listed
+//    (32 edges), history partial sums (BCH rows of BQ blocks, into the member's per-block partial
+//    buffer), their reduction over the blocks in block order (32 edges), T_0^-1 rows, projector
+//    gathers (32 triangles), pseudo-inverse rows, post-processing (32 edges) -- with grid-wide
+//    barriers between the seven phases.  Warps take items from a per-phase counter; the items are listed
 //    longest first, so big scatterers start early and small ones fill the tail.  The row dot
 //    products use the same arithmetic as the per-handle step (simt.h), so every member's
 //    currents equal those of tdcfie_step bit for bit.  Rows per warp, warps per block and blocks
@@ -32,6 +33,7 @@ struct BMember {            // device view of one member handle (FP32, one wave)
     const float* t0inv;     // ne x ne
     const float* pinv;      // nc x nc
     float *E, *H, *ringbuf, *b, *z, *u;
+    double* partial;        // nblk x ne per-block history sums
     const int* pptr;
     const int* pnE;
     const float* px;
@@ -43,11 +45,12 @@ struct BMember {            // device view of one member handle (FP32, one wave)
 };
 
 struct BItem {
-    int member, first, count;
+    int member, first, count, block;   // block: first block of a history item (else 0)
 };
 
-enum { PH_RHS = 0, PH_HIST, PH_SOLVE, PH_PIN, PH_PINV, PH_POUT, NPH };
+enum { PH_RHS = 0, PH_HIST, PH_RED, PH_SOLVE, PH_PIN, PH_PINV, PH_POUT, NPH };
 constexpr int BCH = 8;                 // rows per work item of the row phases
+constexpr int BQ = 4;                  // blocks per history work item
 constexpr uint64_t BWAIT_NS = 2000000000ull;
 
 struct BArgs {
@@ -146,27 +149,31 @@ __device__ __forceinline__ void batch_item(int phase, const BMember& M, const BI
             M.H[e] = hv;
         }
     } else if (phase == PH_HIST) {
-        for (int r0 = it.first; r0 < it.first + it.count; r0 += ROWS) {
-            const int nr = min(ROWS, it.first + it.count - r0);
-            double s[ROWS];
-#pragma unroll
-            for (int i = 0; i < ROWS; ++i) s[i] = 0.0;
-            for (int q = 0; q < M.nblk; ++q) {
-                const float* x;
-                if (q == 0) x = M.E;
-                else if (q == 1) x = M.H;
-                else {
-                    int64_t slot = (n - (q - 1)) % M.ring;
-                    if (slot < 0) slot += M.ring;
-                    x = M.ringbuf + slot * (int64_t)ne;
-                }
+        // per-block partial sums (the arithmetic of k_history_rows), reduced in block order by PH_RED
+        const int q1 = min(M.nblk, it.block + BQ);
+        for (int q = it.block; q < q1; ++q) {
+            const float* x;
+            if (q == 0) x = M.E;
+            else if (q == 1) x = M.H;
+            else {
+                int64_t slot = (n - (q - 1)) % M.ring;
+                if (slot < 0) slot += M.ring;
+                x = M.ringbuf + slot * (int64_t)ne;
+            }
+            for (int r0 = it.first; r0 < it.first + it.count; r0 += ROWS) {
+                const int nr = min(ROWS, it.first + it.count - r0);
                 double acc[ROWS];
                 rows_dot<ROWS>(M.blocks + ((int64_t)q * ne + r0) * ne, ne, nr, ne, x, acc);
-#pragma unroll
-                for (int i = 0; i < ROWS; ++i) s[i] += acc[i];
+                if (lane == 0)
+                    for (int i = 0; i < nr; ++i) M.partial[(int64_t)q * ne + r0 + i] = acc[i];
             }
-            if (lane == 0)
-                for (int i = 0; i < nr; ++i) M.b[r0 + i] = (float)s[i];
+        }
+    } else if (phase == PH_RED) {
+        const int e = it.first + lane;
+        if (lane < it.count) {
+            double v = 0.0;
+            for (int q = 0; q < M.nblk; ++q) v += M.partial[(int64_t)q * ne + e];
+            M.b[e] = (float)v;
         }
     } else if (phase == PH_SOLVE || phase == PH_PINV) {
         const bool solve = phase == PH_SOLVE;
@@ -199,7 +206,7 @@ __device__ __forceinline__ void batch_item(int phase, const BMember& M, const BI
     }
 }
 
-// one MOT step of every member: six phases over the work lists, grid barriers in between
+// one MOT step of every member: seven phases over the work lists, grid barriers in between
 template <int ROWS>
 __global__ void k_batch_step(BArgs a) {
     const int lane = threadIdx.x & 31;
@@ -298,7 +305,7 @@ static int max_blocks_per_sm(int rows, int threads) {
     return e == cudaSuccess ? nb : 0;
 }
 
-// work lists of the six phases, longest items first (by the bytes they stream)
+// work lists of the seven phases, longest items first (by the bytes they stream)
 static cudaError_t build_persistent(tdcfie_batch_t b) {
     const int n = (int)b->hs.size();
     std::vector<BMember> mem(n);
@@ -311,23 +318,25 @@ static cudaError_t build_persistent(tdcfie_batch_t b) {
         M.ne = p->ne; M.nc = p->nc; M.nblk = p->nblk; M.ring = p->ring;
         M.blocks = (const float*)p->blocks; M.t0inv = (const float*)p->t0inv; M.pinv = (const float*)p->pinv;
         M.E = (float*)p->E; M.H = (float*)p->Hv; M.ringbuf = (float*)p->ringbuf;
-        M.b = (float*)p->b; M.z = (float*)p->z; M.u = (float*)p->u;
+        M.b = (float*)p->b; M.z = (float*)p->z; M.u = (float*)p->u; M.partial = (double*)p->partial;
         M.pptr = p->pptr; M.pnE = p->pnE; M.px = (const float*)p->px; M.pc = (const float*)p->pc;
         M.exc = h->dexc; M.m = h->dm; M.dt = h->dt; M.dtt = h->dtt; M.ctl = p->ctl;
         b->hist_bytes += (double)p->nblk * p->ne * p->ne * 4.0;
         for (int e = 0; e < p->ne; e += 32) {
-            const BItem it{s, e, std::min(32, p->ne - e)};
+            const BItem it{s, e, std::min(32, p->ne - e), 0};
             lists[PH_RHS].push_back({(double)p->ne, it});
+            lists[PH_RED].push_back({(double)p->nblk, it});
             lists[PH_POUT].push_back({(double)p->ne, it});
         }
-        for (int c = 0; c < p->nc; c += 32) lists[PH_PIN].push_back({(double)p->nc, BItem{s, c, std::min(32, p->nc - c)}});
+        for (int c = 0; c < p->nc; c += 32) lists[PH_PIN].push_back({(double)p->nc, BItem{s, c, std::min(32, p->nc - c), 0}});
         for (int r = 0; r < p->ne; r += BCH) {
             const int cnt = std::min(BCH, p->ne - r);
-            lists[PH_HIST].push_back({(double)p->nblk * p->ne * cnt, BItem{s, r, cnt}});
-            lists[PH_SOLVE].push_back({(double)p->ne * cnt, BItem{s, r, cnt}});
+            for (int q = 0; q < p->nblk; q += BQ)
+                lists[PH_HIST].push_back({(double)std::min(BQ, p->nblk - q) * p->ne * cnt, BItem{s, r, cnt, q}});
+            lists[PH_SOLVE].push_back({(double)p->ne * cnt, BItem{s, r, cnt, 0}});
         }
         for (int r = 0; r < p->nc; r += BCH)
-            lists[PH_PINV].push_back({(double)p->nc * std::min(BCH, p->nc - r), BItem{s, r, std::min(BCH, p->nc - r)}});
+            lists[PH_PINV].push_back({(double)p->nc * std::min(BCH, p->nc - r), BItem{s, r, std::min(BCH, p->nc - r), 0}});
     }
     std::vector<BItem> all;
     std::vector<size_t> off(NPH);
