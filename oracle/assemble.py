@@ -2,7 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Retarded matrices per time lag k (Dirac testing at t_n of a basis centred at t_{n-k}):
+Retarded matrices per time lag k (Dirac testing at t_n of a basis centred at t_{n-k}); the time
+basis is the paper's hat / C1-quadratic pair (time_order 1) or the shifted quadratic Lagrange
+pair of the remark closing Sec. IV-B (time_order 2, see quad.c):
   S_k[m,n]   = -int int f_m(x).f_n(y) hdot_0(k dt - R) / (4 pi R)           (T^s, Sec. II-A)
   Phi_k[c,c'] = -T0 / (A_c A_c') int_c int_c' q_0(k dt - R) / (4 pi R)        (T^h on q-basis)
   H_k = Sigma Phi_k Sigma^T                                                  (charges div f = Sigma/A)
@@ -29,7 +31,9 @@ _R3_L = np.array([[2 / 3, 1 / 6, 1 / 6], [1 / 6, 2 / 3, 1 / 6], [1 / 6, 1 / 6, 2
 class Operators:
     """All matrices of one mesh and time step (dense, FP64)."""
 
-    def __init__(self, V, F, dt: float, alpha: float = 1.0, K: int | None = None, with_static: bool = True):
+    def __init__(self, V, F, dt: float, alpha: float = 1.0, K: int | None = None, with_static: bool = True,
+                 time_order: int = 1):
+        self.time_order = int(time_order)      # 1: hat / C1-quadratic pair; 2: shifted quadratic Lagrange
         self.topo = topo = Topology(V, F)
         self.bc = bc = BarycentricBC(topo)
         self.dt = float(dt)
@@ -37,7 +41,7 @@ class Operators:
         self.T0 = topo.D                       # T0 = D / c
         self.dtt = self.dt / self.T0           # Delta-tilde t (Sec. III-A)
         self.kappa = 1.0 / self.dt             # kappa = 1/(c dt) (Sec. II-B)
-        self.K = n_lags(topo.D, dt) if K is None else int(K)
+        self.K = n_lags(topo.D, dt, self.time_order) if K is None else int(K)
         self.Lam = topo.Lambda().astype(np.float64)
         self.Sig = topo.Sigma().astype(np.float64)
         self._retarded()
@@ -51,12 +55,16 @@ class Operators:
         L = cquad.lib()
         S = np.zeros((K, ne, ne))
         Phi = np.zeros((K, nc, nc))
-        L.oq_retarded_efie(P(t.V), I(nc), P(t.F), I(ne), P(t.tedge), P(t.tsign), D(self.dt), I(K), D(self.T0),
-                           D(t.D), P(S), P(Phi))
         MM = np.zeros((K, ne, ne))
-        L.oq_retarded_mfie(P(t.V), I(nc), P(t.F), I(ne), P(t.tedge), P(t.tsign),
-                           P(b.fV), I(b.nf), P(b.fF), P(b.fparent), P(b.bc_ptr), P(b.bc_fn), P(b.bc_phi),
-                           D(self.dt), I(K), D(t.D), P(MM))
+        cquad.set_time_order(self.time_order)
+        try:
+            L.oq_retarded_efie(P(t.V), I(nc), P(t.F), I(ne), P(t.tedge), P(t.tsign), D(self.dt), I(K), D(self.T0),
+                               D(t.D), P(S), P(Phi))
+            L.oq_retarded_mfie(P(t.V), I(nc), P(t.F), I(ne), P(t.tedge), P(t.tsign),
+                               P(b.fV), I(b.nf), P(b.fF), P(b.fparent), P(b.bc_ptr), P(b.bc_fn), P(b.bc_phi),
+                               D(self.dt), I(K), D(t.D), P(MM))
+        finally:
+            cquad.set_time_order(1)
         self.S, self.Phi, self.MM = S, Phi, MM
         self.H = np.stack([self.Sig @ Phi[k] @ self.Sig.T for k in range(K)])
 

@@ -52,6 +52,13 @@ def set_rule(nang: int, nrad: int, piece: float):
                        ctypes.c_double(piece))
 
 
+def set_time_order(p: int):
+    """Temporal basis of the retarded matrices: 1 the paper's hat / C1-quadratic pair, 2 the shifted
+    quadratic Lagrange interpolator with its compatible q (quad.c)."""
+    assert p in (1, 2)
+    lib().oq_set_time_order(ctypes.c_int(p))
+
+
 def P(a: np.ndarray):
     """Pointer to a C-contiguous numpy array."""
     assert a.flags["C_CONTIGUOUS"]

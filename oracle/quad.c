@@ -338,19 +338,52 @@ static void polar_far(const double* x, const double* v0, const double* v1, const
     }
 }
 
-/* ---------------- temporal basis (Sec. IV-A) ---------------- */
+/* ---------------- temporal basis (Sec. IV-A) ----------------
+ * Order 1 (the paper's pair): h0 the hat on [-dt, dt], q0 the C1 quadratic on [-dt, 2 dt].
+ * Order 2 (the remark closing Sec. IV-B): h0 the shifted quadratic Lagrange interpolator, i.e.
+ * on [(m-1) dt, m dt] the unknown is interpolated through t_m, t_{m-1}, t_{m-2}; with s = t/dt
+ *   h0 = (s+1)(s+2)/2 on [-1, 0),  1 - s^2 on [0, 1),  (s-1)(s-2)/2 on [1, 2],
+ * and q0 the function with q0' = (h0(t) - h0(t - dt))/dt that vanishes before -dt:
+ *   q0(s) = H(s) - H(s - 1),  H(s) = int_{-1}^{s} h0 (dimensionless),
+ * which is zero again after 3 dt because int h0 = 1. */
+static int TORD = 1;
+void oq_set_time_order(int p) { TORD = (p == 2) ? 2 : 1; }
+int oq_time_order(void) { return TORD; }
+
+static double H2(double s) {          /* int_{-1}^{s} of the order-2 h0 */
+    if (s <= -1.0) return 0.0;
+    if (s < 0.0) { double u = s + 1.0; return u * u * u / 6.0 + u * u / 4.0; }
+    if (s < 1.0) return 5.0 / 12.0 + s - s * s * s / 3.0;
+    if (s < 2.0) { double v = s - 1.0; return 13.0 / 12.0 + v * v * v / 6.0 - v * v / 4.0; }
+    return 1.0;
+}
 static double h0(double t, double dt) {
+    double s = t / dt;
+    if (TORD == 2) {
+        if (s >= -1.0 && s < 0.0) return 0.5 * (s + 1.0) * (s + 2.0);
+        if (s >= 0.0 && s < 1.0) return 1.0 - s * s;
+        if (s >= 1.0 && s <= 2.0) return 0.5 * (s - 1.0) * (s - 2.0);
+        return 0.0;
+    }
     if (t >= -dt && t < 0.0) return 1.0 + t / dt;
     if (t >= 0.0 && t <= dt) return 1.0 - t / dt;
     return 0.0;
 }
 static double h0dot(double t, double dt) {
+    double s = t / dt;
+    if (TORD == 2) {
+        if (s > -1.0 && s < 0.0) return (s + 1.5) / dt;
+        if (s > 0.0 && s < 1.0) return -2.0 * s / dt;
+        if (s > 1.0 && s < 2.0) return (s - 1.5) / dt;
+        return 0.0;
+    }
     if (t > -dt && t < 0.0) return 1.0 / dt;
     if (t > 0.0 && t < dt) return -1.0 / dt;
     return 0.0;
 }
 static double q0(double t, double dt) {
     double s = t / dt;
+    if (TORD == 2) return H2(s) - H2(s - 1.0);
     if (t >= -dt && t < 0.0) return 0.5 * (s + 1.0) * (s + 1.0);
     if (t >= 0.0 && t < dt) return 0.5 - s * s + s;
     if (t >= dt && t <= 2.0 * dt) return 0.5 * (s - 2.0) * (s - 2.0);
@@ -404,7 +437,7 @@ static void ret_cb(void* c, double R, double W, const double* ymx) {
     ret_ctx* r = (ret_ctx*)c;
     for (int k = 0; k < r->K; ++k) {
         double tau = k * r->dt - R;
-        if (tau <= -r->dt || tau >= 2.0 * r->dt) continue;
+        if (tau <= -r->dt || tau >= (TORD + 1) * r->dt) continue;     /* support of q0 */
         double hd = h0dot(tau, r->dt), hv = h0(tau, r->dt), qv = q0(tau, r->dt);
         if (r->want_sp) {
             double fs = -hd / (4.0 * PI * R);

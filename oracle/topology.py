@@ -114,6 +114,7 @@ class Topology:
         return np.zeros_like(r)
 
 
-def n_lags(D: float, dt: float) -> int:
-    """Number of time blocks T_0..T_{K-1}: T_k vanishes once (k - 2) dt >= D (support of q_0)."""
-    return int(np.ceil(D / dt + 2.0))
+def n_lags(D: float, dt: float, order: int = 1) -> int:
+    """Number of time blocks T_0..T_{K-1}: T_k vanishes once (k - order - 1) dt >= D (q_0 is
+    supported on [-dt, (order + 1) dt])."""
+    return int(np.ceil(D / dt + order + 1.0))
