@@ -69,6 +69,9 @@ typedef struct {
     int64_t max_rhs;      /* R: right-hand sides (incident waves) marched together, default 1 */
     void* stream;         /* cudaStream_t; NULL = the legacy default stream */
     int device;           /* CUDA device ordinal, default 0 */
+    int time_order;       /* temporal basis: 1 (default) the hat h_i with the C1 quadratic q_i of
+                             Sec. IV-A; 2 the shifted quadratic Lagrange h_i with the q_i of the
+                             remark closing Sec. IV-B (q_i' = (h_i - h_{i+1})/dt), K one larger */
 } tdcfie_opts;
 
 /* Fill *opts with the defaults above. */
@@ -83,7 +86,7 @@ void tdcfie_default_opts(tdcfie_opts* opts);
  * Builds the edge table (edges = sorted unique vertex pairs, oriented min -> max), the
  * incidence matrices Lambda and Sigma (Sec. II-D), the barycentric refinement and the BC table
  * (Sec. II-C), D (largest vertex distance), T0 = D, and the number of time blocks
- * K = ceil(D/dt + 2).  Host work only (no device is touched until tdcfie_assemble, which
+ * K = ceil(D/dt + time_order + 1).  Host work only (no device is touched until tdcfie_assemble, which
  * uploads the tables).  *out receives the handle.
  * Errors: TDCFIE_E_ARG, TDCFIE_E_MESH, TDCFIE_E_OOM, TDCFIE_E_CUDA.
  */

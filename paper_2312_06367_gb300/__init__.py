@@ -131,7 +131,8 @@ class Solver:
 
     def __init__(self, V, F, dt: float, nt: int, alpha: float = 1.0, precision="fp64", R: int = 1,
                  stream=None, device: int = 0, solver: str = "direct", gmres_tol: float | None = None,
-                 gmres_restart: int | None = None, gmres_maxit: int | None = None, guess: str | None = None):
+                 gmres_restart: int | None = None, gmres_maxit: int | None = None, guess: str | None = None,
+                 time_order: int = 1):
         L = _lib.load()
         self._V = np.ascontiguousarray(V, dtype=np.float64)
         self._F = np.ascontiguousarray(F, dtype=np.int32)
@@ -141,6 +142,7 @@ class Solver:
         o.device = int(device)
         o.stream = ctypes.c_void_p(stream) if stream else None
         o.solver = _SOLVE[solver]
+        o.time_order = int(time_order)
         if gmres_tol is not None:
             o.gmres_tol = float(gmres_tol)
         if gmres_restart is not None:

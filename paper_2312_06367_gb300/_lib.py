@@ -23,7 +23,8 @@ STATUS = {0: "OK", -1: "E_ARG", -2: "E_MESH", -3: "E_OOM", -4: "E_CUDA", -5: "E_
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("solver", ctypes.c_int), ("gmres_tol", ctypes.c_double),
                 ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int), ("guess", ctypes.c_int),
-                ("max_rhs", ctypes.c_int64), ("stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+                ("max_rhs", ctypes.c_int64), ("stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("time_order", ctypes.c_int)]
 
 
 class PlaneWaves(ctypes.Structure):

@@ -39,6 +39,7 @@ extern "C" void tdcfie_default_opts(tdcfie_opts* o) {
     o->max_rhs = 1;
     o->stream = nullptr;
     o->device = 0;
+    o->time_order = 1;
 }
 
 template <class T>
@@ -60,6 +61,7 @@ extern "C" tdcfie_status tdcfie_create(const double* vertices, int64_t nv, const
     tdcfie_default_opts(&o);
     if (opts) o = *opts;
     if (o.precision < TDCFIE_FP64 || o.precision > TDCFIE_FP16X3) return fail(nullptr, TDCFIE_E_ARG, "bad precision");
+    if (o.time_order != 1 && o.time_order != 2) return fail(nullptr, TDCFIE_E_ARG, "time_order must be 1 or 2");
     const bool tensor = o.precision == TDCFIE_BF16X3 || o.precision == TDCFIE_FP16X3;
     if (o.max_rhs < 1 || o.max_rhs > 4096) return fail(nullptr, TDCFIE_E_ARG, "max_rhs out of range [1, 4096]");
     if (tensor && o.max_rhs != 64)
@@ -88,7 +90,7 @@ extern "C" tdcfie_status tdcfie_create(const double* vertices, int64_t nv, const
     h->T0 = h->mesh.D;              // T0 = D / c
     h->dtt = dt / h->T0;            // Delta-tilde t
     h->kappa = 1.0 / dt;            // kappa = 1 / (c dt)
-    h->K = (int)std::ceil(h->mesh.D / dt + 2.0);
+    h->K = (int)std::ceil(h->mesh.D / dt + h->opts.time_order + 1.0);   // q_0 reaches (order + 1) dt
     *out = h;
     return TDCFIE_OK;
 }
@@ -159,12 +161,12 @@ extern "C" tdcfie_status tdcfie_assemble(tdcfie_t h) {
     CK(zalloc(&h->G, ne * ne));
     CK(cudaStreamSynchronize(s));
     t0 = now_s();
-    launch_retarded_efie(h->dm, h->dt, h->K, h->T0, M.D, h->S, h->Phi, s);
+    launch_retarded_efie(h->dm, h->dt, h->K, h->T0, M.D, h->S, h->Phi, h->opts.time_order, s);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     h->asm_s[1] = now_s() - t0;
     t0 = now_s();
-    launch_retarded_mfie(h->dm, h->dt, h->K, M.D, h->MM, s);
+    launch_retarded_mfie(h->dm, h->dt, h->K, M.D, h->MM, h->opts.time_order, s);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     h->asm_s[2] = now_s() - t0;

@@ -71,18 +71,48 @@ __device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y
 __device__ __forceinline__ V3 cross(V3 a, V3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
 __device__ __forceinline__ double nrm(V3 a) { return sqrt(dot(a, a)); }
 
+// Temporal basis (Sec. IV-A).  Order 1: the hat h_0 on [-dt, dt] and the C1 quadratic q_0 on
+// [-dt, 2 dt].  Order 2 (the remark closing Sec. IV-B): the shifted quadratic Lagrange
+// interpolator, s = t / dt,
+//   h_0 = (s+1)(s+2)/2 on [-1, 0),  1 - s^2 on [0, 1),  (s-1)(s-2)/2 on [1, 2],
+// and q_0 with q_0' = (h_0(t) - h_0(t - dt)) / dt, zero before -dt: q_0(s) = H(s) - H(s - 1) with
+// H(s) the integral of h_0 from -1 to s (q_0 vanishes again after 3 dt).
+__constant__ int c_torder;
+
+__device__ __forceinline__ double H2(double s) {
+    if (s <= -1.0) return 0.0;
+    if (s < 0.0) { const double u = s + 1.0; return u * u * u / 6.0 + u * u / 4.0; }
+    if (s < 1.0) return 5.0 / 12.0 + s - s * s * s / 3.0;
+    if (s < 2.0) { const double v = s - 1.0; return 13.0 / 12.0 + v * v * v / 6.0 - v * v / 4.0; }
+    return 1.0;
+}
 __device__ __forceinline__ double h0f(double t, double dt) {
+    if (c_torder == 2) {
+        const double s = t / dt;
+        if (s >= -1.0 && s < 0.0) return 0.5 * (s + 1.0) * (s + 2.0);
+        if (s >= 0.0 && s < 1.0) return 1.0 - s * s;
+        if (s >= 1.0 && s <= 2.0) return 0.5 * (s - 1.0) * (s - 2.0);
+        return 0.0;
+    }
     if (t >= -dt && t < 0.0) return 1.0 + t / dt;
     if (t >= 0.0 && t <= dt) return 1.0 - t / dt;
     return 0.0;
 }
 __device__ __forceinline__ double h0d(double t, double dt) {
+    if (c_torder == 2) {
+        const double s = t / dt;
+        if (s > -1.0 && s < 0.0) return (s + 1.5) / dt;
+        if (s > 0.0 && s < 1.0) return -2.0 * s / dt;
+        if (s > 1.0 && s < 2.0) return (s - 1.5) / dt;
+        return 0.0;
+    }
     if (t > -dt && t < 0.0) return 1.0 / dt;
     if (t > 0.0 && t < dt) return -1.0 / dt;
     return 0.0;
 }
 __device__ __forceinline__ double q0f(double t, double dt) {
     const double s = t / dt;
+    if (c_torder == 2) return H2(s) - H2(s - 1.0);
     if (t >= -dt && t < 0.0) return 0.5 * (s + 1.0) * (s + 1.0);
     if (t >= 0.0 && t < dt) return 0.5 - s * s + s;
     if (t >= dt && t <= 2.0 * dt) return 0.5 * (s - 2.0) * (s - 2.0);
@@ -358,7 +388,7 @@ struct EfieAcc {
     __device__ void operator()(double R, double W, V3 ymx) {
         for (int i = 0; i < nk; ++i) {
             const double tau = (k0 + i) * dt - R;
-            if (tau <= -dt || tau >= 2.0 * dt) continue;
+            if (tau <= -dt || tau >= (c_torder + 1) * dt) continue;      // support of q_0
             const double inv = 1.0 / (4.0 * M_PI * R);
             const double fs = -h0d(tau, dt) * inv;
             s0[i] += W * fs;
@@ -388,7 +418,7 @@ __global__ void k_retarded_efie(DevMesh m, double dt, int K, double T0, double* 
     const int nb = make_breaks(ad, hi, dt, brk, overflow);
     int klo = (int)floor(lo / dt) - 1;
     if (klo < 0) klo = 0;
-    int khi = (int)ceil(hi / dt) + 2;
+    int khi = (int)ceil(hi / dt) + c_torder + 1;
     if (khi > K - 1) khi = K - 1;
     const V3 wv[3] = {w0, w1, w2}, vv[3] = {v0, v1, v2};
     for (int k0 = klo; k0 <= khi; k0 += LAGW) {
@@ -423,7 +453,7 @@ struct MfieAcc {
     __device__ void operator()(double R, double W, V3 ymx) {
         for (int i = 0; i < nk; ++i) {
             const double tau = (k0 + i) * dt - R;
-            if (tau <= -dt || tau >= dt) continue;
+            if (tau <= -dt || tau >= c_torder * dt) continue;            // support of h_0
             const double fm = (h0f(tau, dt) / R + h0d(tau, dt)) / (4.0 * M_PI * R * R);
             m1[i][0] += W * fm * ymx.x; m1[i][1] += W * fm * ymx.y; m1[i][2] += W * fm * ymx.z;
         }
@@ -450,7 +480,7 @@ __global__ void k_retarded_mfie(DevMesh m, double dt, int K, double* __restrict_
     const int nb = make_breaks(ad, hi, dt, brk, overflow);
     int klo = (int)floor(lo / dt) - 1;
     if (klo < 0) klo = 0;
-    int khi = (int)ceil(hi / dt) + 2;
+    int khi = (int)ceil(hi / dt) + c_torder + 1;
     if (khi > K - 1) khi = K - 1;
     const V3 wv[3] = {w0, w1, w2}, vv[3] = {v0, v1, v2};
     for (int k0 = klo; k0 <= khi; k0 += LAGW) {
@@ -635,15 +665,17 @@ static int* overflow_flag(cudaStream_t s) {
 static unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 void launch_retarded_efie(const DevMesh& m, double dt, int K, double T0, double D, double* S, double* Phi,
-                          cudaStream_t s) {
+                          int order, cudaStream_t s) {
     (void)D;
+    cudaMemcpyToSymbolAsync(c_torder, &order, sizeof(int), 0, cudaMemcpyHostToDevice, s);
     int* of = overflow_flag(s);
     const int64_t n = (int64_t)m.nc * 7 * m.nc;
     k_retarded_efie<<<blocks(n, 128), 128, 0, s>>>(m, dt, K, T0, S, Phi, of);
 }
 
-void launch_retarded_mfie(const DevMesh& m, double dt, int K, double D, double* MM, cudaStream_t s) {
+void launch_retarded_mfie(const DevMesh& m, double dt, int K, double D, double* MM, int order, cudaStream_t s) {
     (void)D;
+    cudaMemcpyToSymbolAsync(c_torder, &order, sizeof(int), 0, cudaMemcpyHostToDevice, s);
     int* of = overflow_flag(s);
     const int64_t n = (int64_t)m.nf * 3 * m.nc;
     k_retarded_mfie<<<blocks(n, 128), 128, 0, s>>>(m, dt, K, MM, of);

@@ -61,8 +61,8 @@ void set_rule_tables(const RuleTables& r, cudaStream_t s);
 // symmetric degree-5 rule on a triangle: per point barycentric (a, b, c) and weight (sum 1)
 void triangle_rule7(double r7[7][4]);
 void launch_retarded_efie(const DevMesh& m, double dt, int K, double T0, double D, double* S, double* Phi,
-                          cudaStream_t s);
-void launch_retarded_mfie(const DevMesh& m, double dt, int K, double D, double* MM, cudaStream_t s);
+                          int order, cudaStream_t s);
+void launch_retarded_mfie(const DevMesh& m, double dt, int K, double D, double* MM, int order, cudaStream_t s);
 void launch_static(const DevMesh& m, double kappa, double* Zs, double* Psi, double* M, double* G, cudaStream_t s);
 
 // ---------------------------------------------------------------- dense FP64 helpers (linalg.cu)

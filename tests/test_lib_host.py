@@ -80,3 +80,16 @@ def test_rejects_bad_meshes(lib):
         Solver(V, F, dt=-1.0, nt=5)
     with pytest.raises(TdcfieError, match="E_UNSUPPORTED"):
         Solver(V, F, dt=0.3, nt=5, precision="fp32", R=16)
+
+
+def test_time_order_sets_the_lag_count(lib):
+    """K = ceil(D/dt + order + 1): q_0 is supported on [-dt, (order + 1) dt] (host only)."""
+    from oracle.topology import Topology, n_lags
+    from paper_2312_06367_gb300 import Solver, TdcfieError
+    V, F = meshes.icosphere(1)
+    D = Topology(V, F).D
+    for order in (1, 2):
+        s = Solver(V, F, dt=0.3, nt=5, time_order=order)
+        assert s.K == n_lags(D, 0.3, order) == int(np.ceil(D / 0.3 + order + 1))
+    with pytest.raises(TdcfieError, match="E_ARG"):
+        Solver(V, F, dt=0.3, nt=5, time_order=3)
