@@ -81,3 +81,18 @@ def meshes_D():
     from oracle.topology import Topology
     V, F = meshes.icosphere(1)
     return Topology(V, F).D
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_blocks_vanish_beyond_the_lag_count(order):
+    """Assembled with two extra lags, the retarded blocks past K = ceil(D/dt + order + 1) are zero
+    and the last one inside is not: the support of q_0 ends at (order + 1) dt."""
+    from oracle.assemble import Operators
+    from oracle.topology import Topology, n_lags
+    V, F = meshes.icosphere(1)
+    dt = 0.4
+    K = n_lags(Topology(V, F).D, dt, order)
+    ops = Operators(V, F, dt=dt, K=K + 2, with_static=False, time_order=order)
+    for k in (K, K + 1):
+        assert not ops.S[k].any() and not ops.MM[k].any() and not ops.Phi[k].any()
+    assert ops.Phi[K - 1].any()
